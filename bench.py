@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Benchmark: assembly of 3D Nedelec K and M into CSR on GB300.
+
+One step = one ef_assemble call (element matrices in closed form + the
+fixed-order sum into CSR) on the 3D Nedelec workload: the unit cube as a
+64^3 grid of cubes split into 6 tetrahedra (1,572,864 tets), interior nodes
+jittered by +-0.2h (seed 2), per-element coefficient log-uniform in
+[0.1, 10]. The plan (topology + pattern) is built before timing, as in a
+shape-optimisation loop where only coordinates and coefficients change.
+
+Prints one JSON line: throughput (M elements / s), e2e through the host-buffer
+C-ABI call, the HBM and FP64 rooflines of the step's kernel(s), the clocks
+seen while timing, and the CPU oracle timed on this host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the plain FP64 quadrature assembler
+that the tests compare against) on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank assembles its own replica (the single-mesh
+path is not sharded: replicas only) and rank 0 reports the job total.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1409_4618_gb300 import meshgen as mg  # noqa: E402
+
+WORKLOAD = {"name": "ned3d_kuhn64_jitter0.2", "kind": 2, "dim": 3, "n": 64, "jitter": 0.2, "seed": 2}
+METRIC = "M elements/s assembled to CSR (K+M), % HBM roofline; batched & adjoint vs plain"
+UNIT = "Melem/s"
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (non-tensor) nominal, FMA = 2 flops
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _workload():
+    w = WORKLOAD
+    nodes, elems = mg.kuhn_cube(w["n"], w["jitter"], w["seed"])
+    coeff = mg.log_uniform_coeff(w["seed"], elems.shape[0])
+    return nodes, elems, coeff
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, val in zip(names, r[5:9]):
+                if "Active" in val and "Not" not in val:
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def fp64_ops_per_element(kind: int, dim: int) -> int:
+    """FP64 pipe operations (DADD/DMUL/DFMA each 1) of one element's local
+    matrices in the closed forms of csrc/ef_element.cuh, counted from the
+    source; the reciprocal / rsqrt is counted as 10."""
+    if (kind, dim) == (2, 3):
+        # B 9, H 18, adj(H) 12, det H 3, rsqrt 10, scales 2, K: 6 + 15, M: 7 + 6 + 8 + 6*3 + 15*3
+        return 9 + 18 + 12 + 3 + 10 + 2 + 21 + 7 + 6 + 8 + 18 + 45
+    if (kind, dim) == (1, 3):
+        return 9 + 18 + 9 + 10 + 1 + 6 + 5 + 4 + 3 + 3 + 3 + 15 + 1
+    return 40
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    w = WORKLOAD
+    # bounded sample of the same recipe per step, sized so that the whole run
+    # stays near one minute of CPU time whatever K and W are (~8e6 tets in total)
+    ns = int(max(4, min(64, (8e6 / (6 * (args.steps + args.warmup))) ** (1 / 3))))
+    nodes, elems = mg.kuhn_cube(ns, w["jitter"], w["seed"])
+    coeff = mg.log_uniform_coeff(w["seed"], elems.shape[0])
+    for _ in range(args.warmup):
+        oracle.assemble(w["kind"], w["dim"], nodes, elems, coeff)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.assemble(w["kind"], w["dim"], nodes, elems, coeff)
+    dt = time.perf_counter() - t0
+    value = args.steps * elems.shape[0] / dt / 1e6
+    sample = f"{ns}^3 cubes x 6 tets ({elems.shape[0]} tets) of the same jitter/coefficient recipe per step, end to end"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "sample_tets": int(elems.shape[0])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline():
+    """The oracle as it stands, timed on this host: the full workload, one thread."""
+    import oracle
+
+    oracle.build()
+    nodes, elems, coeff = _workload()
+    t0 = time.perf_counter()
+    oracle.assemble(WORKLOAD["kind"], WORKLOAD["dim"], nodes, elems, coeff)
+    dt = time.perf_counter() - t0
+    return {"value": elems.shape[0] / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the full workload ({elems.shape[0]} tets), topology + pattern + quadrature assembly, "
+                      f"single thread, {dt:.1f} s"}
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    nodes, elems, coeff = _workload()
+    w = WORKLOAD
+    tn = torch.from_numpy(nodes).to(dev)
+    tc = torch.from_numpy(coeff).to(dev)
+    plan = ef.Plan(w["kind"], w["dim"], nodes.shape[0], torch.from_numpy(elems).to(dev))
+    T, V, nnz = elems.shape[0], nodes.shape[0], plan.nnz
+    K = torch.empty(nnz, dtype=torch.float64, device=dev)
+    M = torch.empty(nnz, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    path = args.path
+    if path.startswith("blocked"):
+        plan.set_block(int(path[len("blocked"):]))
+
+    def step():
+        if path == "two_pass":
+            ef.ef_assemble_two_pass(plan.handle, tn, tc, K, M, stream)
+        else:
+            ef.ef_assemble(plan.handle, tn, tc, K, M, stream)
+
+    for _ in range(args.warmup):
+        step()
+    plan.check()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device time by CUDA events on the launching stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    plan.check()
+    ms_t = torch.tensor([ms], device=dev)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_step = ms / args.steps
+    value = ws * T * args.steps / (ms / 1e3) / 1e6
+
+    # ---- end to end through the host-buffer C-ABI call
+    hn = torch.from_numpy(nodes).pin_memory()
+    hc = torch.from_numpy(coeff).pin_memory()
+    hK = torch.empty(nnz, dtype=torch.float64, pin_memory=True)
+    hM = torch.empty(nnz, dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 20))
+    plan.assemble_host(hn, hc, hK, hM)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        plan.assemble_host(hn, hc, hK, hM)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e = {"value": ws * T / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(hn.numel() * 8 + hc.numel() * 8),
+           "d2h_bytes_per_step": int(2 * nnz * 8)}
+
+    # ---- rooflines of the step
+    peaks, src = _peaks()
+    alg_bytes = 16 * T + 8 * T + 8 * w["dim"] * V + 16 * nnz
+    achieved_gbs = alg_bytes / (ms_step / 1e3) / 1e9
+    n_pairs = 21
+    U = (nnz + plan.n_dofs) // 2
+    fp64_ops = T * fp64_ops_per_element(w["kind"], w["dim"]) + 2 * (T * n_pairs - U)
+    achieved_ops = fp64_ops / (ms_step / 1e3) / 1e12
+    fp64_peak_ops = FP64_NOMINAL_TFLOPS / 2.0    # T FP64 pipe ops / s (one DFMA = 2 flops)
+    roofline = {
+        "bound": "alu", "unit": "T fp64-ops/s", "achieved": achieved_ops, "peak": fp64_peak_ops,
+        "frac": achieved_ops / fp64_peak_ops, "traffic": None,
+        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s / 2 (DADD, DMUL, DFMA = 1 op each)",
+        "kernel": "ef_assemble step (" + path + ")",
+        "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved_gbs / peaks["hbm_gbs"], "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_step": int(alg_bytes), "bytes_per_elem": alg_bytes / T},
+    }
+    info = plan.info()
+    launches = (2 if path == "two_pass" else info["assemble_launches"]) * args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "elements": T, "nodes": V, "dofs": plan.n_dofs, "nnz": nnz,
+                   "path": path, "plan": info, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": f"no flush: each step moves {alg_bytes / 1e6:.0f} MB (algorithmic) > 129 MB L2"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--path", default="default", choices=["default", "two_pass", "blocked128", "blocked256"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

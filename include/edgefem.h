@@ -1,0 +1,215 @@
+/*
+ * edgefem.h -- C ABI of libedgefem.so: GPU assembly of lowest-order
+ * Raviart-Thomas (H(div)) and Nedelec first-kind (H(curl)) mass and
+ * div/curl stiffness matrices on triangle and tetrahedron meshes into
+ * global CSR matrices, after I. Anjam and J. Valdman, "Fast MATLAB assembly
+ * of FEM matrices in 2D and 3D: Edge elements" (arXiv 1409.4618).
+ *
+ * The matrices (Sec. 2.4):
+ *   M_ij = int_Omega sigma eta_i . eta_j,
+ *   K_ij = int_Omega sigma div eta_i div eta_j        (RT0),
+ *   K_ij = int_Omega sigma curl eta_i . curl eta_j    (Nedelec, curl scalar in 2D),
+ * where eta_i are the global basis functions built from the reference bases
+ * of Sec. 2.1-2.2 with the Piola maps of Eqs. RT0piola and Ned0piola1-3 and
+ * the orientation signs of Sec. 2.3, and sigma is a per-element coefficient
+ * (1 if none is given) that scales both K and M. The 3D RT0 basis is used
+ * exactly as printed in Sec. 2.1 (its face fluxes are 1/2).
+ *
+ * Conventions shared by every entry point:
+ *   - Meshes: nodes are V x dim doubles, row-major (x, y[, z] per node);
+ *     elements are T x (dim+1) int32 node ids, row-major, 0-based. Any
+ *     orientation (det B_K of either sign) is allowed (Sec. 2.3).
+ *   - Global DOF numbering (Sec. 3, "row indices of edges2nodes /
+ *     faces2nodes"): the DOFs are the distinct edges (faces for 3D RT0) ranked
+ *     lexicographically by their sorted global node ids.
+ *   - Local DOF order and directions (Fig. 1): 2D edge k lies opposite local
+ *     node k and runs (1,2), (2,0), (0,1); 3D edges run (0,1), (0,2), (0,3),
+ *     (1,2), (2,3), (3,1); 3D face k is opposite local node 3-k.
+ *   - Orientation signs (Sec. 2.3): an edge DOF gets +1 iff the global id of
+ *     its tail exceeds that of its head (the rule Sec. 3 states for 2D,
+ *     applied to every edge); a face DOF gets -parity of the permutation that
+ *     lists its three nodes by ascending global id followed by the opposite
+ *     node. Sign bit k of an element is set iff its sign is -1.
+ *   - CSR: 0-based, both triangles stored, columns ascending within a row,
+ *     int64 row pointers, int32 column indices. The pattern holds every pair
+ *     of DOFs that share an element; entries that happen to be zero are kept.
+ *     K and M share one pattern.
+ *   - Pointers named d_* are CUDA device pointers, h_* host pointers. The
+ *     caller owns every buffer it passes; the library owns plan internals.
+ *     `stream` is a cudaStream_t (NULL = the legacy default stream); all
+ *     device work of a call is ordered on it.
+ *   - Every call returns EF_OK (0) or a negative status; nothing is written
+ *     to caller buffers when an argument check fails. There is no CPU
+ *     fallback: without a CUDA device every compute call returns EF_ERR_CUDA.
+ *   - All floating-point arithmetic is IEEE FP64. Sums of element
+ *     contributions are formed in a fixed order (ascending element id within
+ *     a nonzero), without floating-point atomics: results are bitwise
+ *     reproducible from run to run.
+ */
+#ifndef EDGEFEM_H
+#define EDGEFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EF_OK 0
+#define EF_ERR_ARG (-1)          /* bad pointer, size, kind or dim; repeated node in an element */
+#define EF_ERR_RANGE (-2)        /* node id outside [0, n_nodes) */
+#define EF_ERR_DEGENERATE (-3)   /* an element has det B_K = 0 */
+#define EF_ERR_KEY_OVERFLOW (-4) /* 3D RT0 face keys need n_nodes^3 < 2^64 (n_nodes <= 2642245) */
+#define EF_ERR_OOM (-5)          /* device allocation failed */
+#define EF_ERR_CUDA (-6)         /* a CUDA runtime call failed (see ef_last_error) */
+#define EF_ERR_TIMEOUT (-7)      /* a bounded device-side wait gave up */
+#define EF_ERR_SIZE (-8)         /* mesh beyond the 32-bit index limits stated per call */
+
+typedef enum { EF_RT0 = 1, EF_NED1 = 2 } ef_kind;
+
+typedef struct ef_plan ef_plan;
+
+/*
+ * Build the per-mesh plan: topology (edges / faces, their global numbering
+ * and the per-element orientation signs; Sec. 3 "get_edges / get_faces /
+ * signs_edges / signs_faces") and the CSR pattern with the map from every
+ * element contribution to its nonzero. Depends on the connectivity only,
+ * never on coordinates or coefficients; reused by every ef_assemble.
+ *   kind: EF_RT0 or EF_NED1; dim: 2 or 3.
+ *   d_elems: n_elems x (dim+1) int32, device; copied, may be freed after.
+ * Synchronises `stream` (the sizes of the plan depend on the data).
+ * Errors: EF_ERR_ARG, EF_ERR_RANGE, EF_ERR_KEY_OVERFLOW, EF_ERR_OOM,
+ *   EF_ERR_CUDA, EF_ERR_SIZE (n_elems * nloc(nloc+1)/2 >= 2^32 or nnz >= 2^32).
+ * On success *out owns device memory until ef_plan_destroy.
+ */
+int ef_plan_create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, void* stream,
+                   ef_plan** out);
+
+/* Number of global DOFs (rows) and CSR nonzeros of the plan. Host only. */
+int ef_plan_sizes(const ef_plan* plan, int64_t* n_dofs, int64_t* nnz);
+
+/* Plan facts for diagnostics and benchmarks (host only): counts and how
+ * ef_assemble runs. Not part of the paper's method. */
+typedef struct {
+    int64_t n_dofs, nnz;
+    int64_t n_upper;              /* nonzeros with row <= column */
+    int64_t n_contrib;            /* element contributions: n_elems * nloc (nloc+1) / 2 */
+    int32_t assemble_launches;    /* kernel launches made by one ef_assemble */
+    int32_t fused_block;          /* elements per CTA of the element-block path if selected, else 0 */
+    int64_t fused_blocks;
+    int64_t fused_partial;        /* element-block path: contributions summed by the fix-up */
+    int32_t pipeline_chunks;      /* element chunks of the pipelined path (1: not pipelined) */
+} ef_plan_info_t;
+int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info);
+
+/* Select how ef_assemble runs. block = 0: the pipelined two-pass path
+ * (default). block = 128 or 256: the element-block path, one CTA per block of
+ * `block` elements that keeps its local matrices in shared memory, completes
+ * the nonzeros lying wholly in the block and hands the others to a fix-up
+ * kernel. Results are identical bit for bit (same summation order); only
+ * speed differs. Synchronises `stream` and allocates when building the
+ * block schedule. Errors: EF_ERR_ARG, EF_ERR_OOM. */
+int ef_plan_set_block(ef_plan* plan, int block, void* stream);
+
+/* Copy the CSR pattern into caller buffers: d_rowptr [n_dofs+1] int64,
+ * d_colidx [nnz] int32 (device). Asynchronous on `stream`. */
+int ef_plan_pattern(const ef_plan* plan, int64_t* d_rowptr, int32_t* d_colidx, void* stream);
+
+/* Copy the topology into caller buffers (any pointer may be NULL to skip):
+ * d_elem2dof [n_elems x nloc] int32 (elems2edges / elems2faces of Sec. 3),
+ * d_signbits [n_elems] uint8 (bit k set iff local DOF k has sign -1),
+ * d_dof2nodes [n_dofs x 2] (edges) or [n_dofs x 3] (faces) int32, ascending
+ * node ids (edges2nodes / faces2nodes). Asynchronous on `stream`. */
+int ef_plan_topology(const ef_plan* plan, int32_t* d_elem2dof, uint8_t* d_signbits, int32_t* d_dof2nodes,
+                     void* stream);
+
+/*
+ * Assemble K and M values into caller-owned CSR value arrays (pattern of
+ * ef_plan_pattern): local matrices by the closed forms of the Sec. 2.4
+ * integrals on every element, then the fixed-order sum into each nonzero.
+ * The element kernel runs in chunks on `stream`; the sums of the nonzeros a
+ * chunk completes run on a plan-owned stream while the next chunk computes
+ * (joined back into `stream` by events, so the call is one unit of work on
+ * `stream` and captures into a CUDA graph as a fork/join).
+ *   d_nodes: n_nodes x dim doubles; d_coeff: n_elems doubles or NULL (= 1);
+ *   d_Kval, d_Mval: nnz doubles each (overwritten).
+ * Asynchronous; allocates nothing; no host synchronisation (capturable in a
+ * CUDA graph). A degenerate element (det B_K = 0) is reported by the next
+ * ef_plan_check, not by this call; its contributions are then non-finite.
+ * Calls on one plan that overlap on the GPU race on the plan's scratch.
+ */
+int ef_assemble(const ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
+                void* stream);
+
+/* Same sums as ef_assemble, in two separate kernels: an element kernel writes
+ * every local matrix to plan scratch, then one thread per upper nonzero sums
+ * its contributions. Same values bit for bit (same summation order). */
+int ef_assemble_two_pass(const ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval,
+                         double* d_Mval, void* stream);
+
+/*
+ * End-to-end form for host data: copies h_nodes (n_nodes x dim) and h_coeff
+ * (n_elems, or NULL) to plan-owned device staging buffers, assembles, and
+ * copies K and M values back into h_Kval / h_Mval (nnz doubles each). Host
+ * buffers should be pinned for asynchronous copies. Synchronises `stream`
+ * before returning and reports degenerate elements (EF_ERR_DEGENERATE).
+ * The first call allocates the staging buffers.
+ */
+int ef_assemble_host(ef_plan* plan, const double* h_nodes, const double* h_coeff, double* h_Kval, double* h_Mval,
+                     void* stream);
+
+/* Synchronise `stream`, then read and clear the plan's device status word:
+ * EF_ERR_DEGENERATE if an element with det B_K = 0 was met since the last
+ * check, EF_ERR_TIMEOUT if a bounded wait gave up, else EF_OK. */
+int ef_plan_check(ef_plan* plan, void* stream);
+
+/* Free the plan (device memory included). Synchronises the device. NULL is a no-op. */
+void ef_plan_destroy(ef_plan* plan);
+
+/*
+ * Adjoint of the quadratic form
+ *   J(x, sigma) = u^T K(x, sigma) u + v^T M(x, sigma) v
+ *              = sum_K sigma_K (u_K^T Khat_K u_K + v_K^T Mhat_K v_K),
+ * u_K = u[elem2dof(K,:)], Khat_K / Mhat_K the signed unit-coefficient local
+ * matrices (Sec. 2.4). Writes d_J (1 double), d_grad_nodes (n_nodes x dim,
+ * dJ/dx) and d_grad_coeff (n_elems, dJ/dsigma); any output may be NULL to
+ * skip it. Element geometry is recomputed, nothing is stored per element.
+ * Nedelec 3D only (other kinds return EF_ERR_ARG). d_u, d_v: n_dofs doubles.
+ * Asynchronous; no allocation; fixed summation order.
+ */
+int ef_adjoint(const ef_plan* plan, const double* d_nodes, const double* d_coeff, const double* d_u,
+               const double* d_v, double* d_J, double* d_grad_nodes, double* d_grad_coeff, void* stream);
+
+/* ---- one-shot convenience calls ------------------------------------------ */
+
+typedef struct {
+    int64_t n_dofs;
+    int64_t nnz;
+    int64_t* d_rowptr; /* n_dofs + 1, device, library-allocated */
+    int32_t* d_colidx; /* nnz, device */
+    double* d_K;       /* nnz, device */
+    double* d_M;       /* nnz, device */
+} ef_csr;
+
+/* Plan + assemble + check in one call for RT0 (rt0_) or Nedelec (ned_)
+ * elements; dim 2 or 3. The CSR arrays in *out are allocated by the library
+ * and released with ef_csr_free. Synchronises `stream`. Errors as
+ * ef_plan_create, plus EF_ERR_DEGENERATE. */
+int rt0_assemble(int dim, const double* d_nodes, int64_t n_nodes, const int32_t* d_elems, int64_t n_elems,
+                 const double* d_coeff, ef_csr* out, void* stream);
+int ned_assemble(int dim, const double* d_nodes, int64_t n_nodes, const int32_t* d_elems, int64_t n_elems,
+                 const double* d_coeff, ef_csr* out, void* stream);
+void ef_csr_free(ef_csr* csr);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+
+/* Static text for a status code. */
+const char* ef_status_string(int status);
+/* Text of the last CUDA error seen by this thread inside the library ("" if none). */
+const char* ef_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EDGEFEM_H */

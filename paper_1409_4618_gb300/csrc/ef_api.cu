@@ -1,0 +1,325 @@
+// C ABI entry points of libedgefem (declared in include/edgefem.h).
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "ef_internal.cuh"
+
+using namespace ef;
+
+namespace {
+
+void free_plan_memory(ef_plan* p)
+{
+    void* ptrs[] = {p->d_elems,     p->d_elem2dof,   p->d_signbits,  p->d_dof2nodes,   p->d_rowptr,
+                    p->d_colidx,    p->d_seg,        p->d_perm,      p->d_pos_up,      p->d_pos_lo,
+                    p->d_local,     p->d_status,     p->d_fb_slot_off, p->d_fb_sinfo, p->d_fb_cidx,
+                    p->d_fb_posA,   p->d_fb_posB,    p->d_px_uid,
+                    p->d_stage_nodes, p->d_stage_coeff, p->d_stage_K, p->d_stage_M,
+                    p->d_node_off,  p->d_node_inc,   p->d_adj_part,  p->d_adj_jpart, p->d_uorder};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+int plan_args(int kind, int dim, int64_t n_nodes, int64_t n_elems, const void* d_elems)
+{
+    if ((kind != EF_RT0 && kind != EF_NED1) || (dim != 2 && dim != 3)) return EF_ERR_ARG;
+    if (n_nodes < 0 || n_elems < 0 || (n_elems > 0 && !d_elems)) return EF_ERR_ARG;
+    if (n_nodes > (int64_t)INT32_MAX) return EF_ERR_SIZE;
+    const int v = variant_of(kind, dim);
+    const int64_t lim = (int64_t)1 << 32;
+    if (n_elems >= lim / npair_of(v)) return EF_ERR_SIZE;
+    if (v == RT3 && n_nodes > 2642245) return EF_ERR_KEY_OVERFLOW;  // 2642245^3 < 2^64
+    return EF_OK;
+}
+
+int create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, cudaStream_t s, ef_plan** out)
+{
+    ef_plan* p = (ef_plan*)calloc(1, sizeof(ef_plan));
+    if (!p) return EF_ERR_OOM;
+    p->kind = kind;
+    p->dim = dim;
+    p->variant = variant_of(kind, dim);
+    p->nv = dim + 1;
+    p->nl = nloc_of(p->variant);
+    p->np = npair_of(p->variant);
+    p->ent = ent_nodes_of(p->variant);
+    p->V = n_nodes;
+    p->T = n_elems;
+    int st = EF_OK;
+    do {
+        cudaError_t e = cudaMalloc((void**)&p->d_status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_elems, (size_t)(n_elems > 0 ? n_elems : 1) * p->nv * 4);
+        if (e != cudaSuccess) {
+            set_last_error("cudaMalloc", e);
+            st = e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;
+            break;
+        }
+        e = cudaMemsetAsync(p->d_status, 0, sizeof(int), s);
+        if (e == cudaSuccess && n_elems > 0)
+            e = cudaMemcpyAsync(p->d_elems, d_elems, (size_t)n_elems * p->nv * 4, cudaMemcpyDefault, s);
+        if (e != cudaSuccess) {
+            set_last_error("cudaMemcpyAsync(elems)", e);
+            st = EF_ERR_CUDA;
+            break;
+        }
+        if ((st = validate_elems(p, s)) != EF_OK) break;
+        if ((st = build_topology(p, s)) != EF_OK) break;
+        if ((st = build_pattern(p, s)) != EF_OK) break;
+        e = cudaMalloc((void**)&p->d_local, (size_t)(p->T > 0 ? p->T : 1) * p->np * 2 * sizeof(double));
+        if (e != cudaSuccess) {
+            set_last_error("cudaMalloc(local)", e);
+            st = EF_ERR_OOM;
+            break;
+        }
+        if ((st = build_scatter_order(p, s)) != EF_OK) break;
+        if ((st = build_adjoint(p, s)) != EF_OK) break;
+    } while (0);
+    if (st != EF_OK) {
+        cudaStreamSynchronize(s);
+        destroy_pipeline(p);
+        free_plan_memory(p);
+        free(p);
+        return st;
+    }
+    *out = p;
+    return EF_OK;
+}
+
+int assemble_checks(const ef_plan* plan, const double* nodes, double* K, double* M)
+{
+    if (!plan) return EF_ERR_ARG;
+    if (plan->T > 0 && (!nodes || !K || !M)) return EF_ERR_ARG;
+    return EF_OK;
+}
+
+int one_shot(int kind, int dim, const double* d_nodes, int64_t n_nodes, const int32_t* d_elems, int64_t n_elems,
+             const double* d_coeff, ef_csr* out, void* stream)
+{
+    if (!out) return EF_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    if (n_elems > 0 && !d_nodes) return EF_ERR_ARG;
+    ef_plan* p = nullptr;
+    int st = ef_plan_create(kind, dim, n_nodes, n_elems, d_elems, stream, &p);
+    if (st != EF_OK) return st;
+    ef_csr c;
+    memset(&c, 0, sizeof(c));
+    c.n_dofs = p->N;
+    c.nnz = p->nnz;
+    cudaError_t e = cudaMalloc((void**)&c.d_rowptr, (size_t)(p->N + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.d_colidx, (size_t)(p->nnz > 0 ? p->nnz : 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.d_K, (size_t)(p->nnz > 0 ? p->nnz : 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.d_M, (size_t)(p->nnz > 0 ? p->nnz : 1) * 8);
+    if (e != cudaSuccess) {
+        set_last_error("cudaMalloc(csr)", e);
+        st = EF_ERR_OOM;
+    }
+    if (st == EF_OK) st = ef_plan_pattern(p, c.d_rowptr, c.d_colidx, stream);
+    if (st == EF_OK) st = ef_assemble(p, d_nodes, d_coeff, c.d_K, c.d_M, stream);
+    if (st == EF_OK) st = ef_plan_check(p, stream);
+    ef_plan_destroy(p);
+    if (st != EF_OK) {
+        ef_csr_free(&c);
+        return st;
+    }
+    *out = c;
+    return EF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ef_plan_create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, void* stream,
+                   ef_plan** out)
+{
+    if (!out) return EF_ERR_ARG;
+    *out = nullptr;
+    int st = plan_args(kind, dim, n_nodes, n_elems, d_elems);
+    if (st != EF_OK) return st;
+    return create(kind, dim, n_nodes, n_elems, d_elems, (cudaStream_t)stream, out);
+}
+
+int ef_plan_sizes(const ef_plan* plan, int64_t* n_dofs, int64_t* nnz)
+{
+    if (!plan) return EF_ERR_ARG;
+    if (n_dofs) *n_dofs = plan->N;
+    if (nnz) *nnz = plan->nnz;
+    return EF_OK;
+}
+
+int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info)
+{
+    if (!plan || !info) return EF_ERR_ARG;
+    memset(info, 0, sizeof(*info));
+    info->n_dofs = plan->N;
+    info->nnz = plan->nnz;
+    info->n_upper = plan->U;
+    info->n_contrib = plan->T * plan->np;
+    if (plan->T == 0)
+        info->assemble_launches = 0;
+    else if (plan->use_blocked && plan->fb_nblocks > 0)
+        info->assemble_launches = plan->n_px > 0 ? 2 : 1;
+    else
+        info->assemble_launches = plan->pc_chunks > 1 ? 2 * plan->pc_chunks : 2;
+    info->fused_block = plan->use_blocked ? plan->fb_block : 0;
+    info->pipeline_chunks = plan->pc_chunks;
+    info->fused_blocks = plan->fb_nblocks;
+    info->fused_partial = plan->n_partial;
+    return EF_OK;
+}
+
+int ef_plan_set_block(ef_plan* plan, int block, void* stream)
+{
+    if (!plan) return EF_ERR_ARG;
+    if (block == 0) {
+        plan->use_blocked = 0;
+        return EF_OK;
+    }
+    if (!fused_block_supported(block)) return EF_ERR_ARG;
+    EF_TRY(build_fused_block(plan, block, (cudaStream_t)stream));
+    plan->use_blocked = 1;
+    return EF_OK;
+}
+
+int ef_plan_pattern(const ef_plan* plan, int64_t* d_rowptr, int32_t* d_colidx, void* stream)
+{
+    if (!plan || !d_rowptr || (plan->nnz > 0 && !d_colidx)) return EF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    EF_CUDA(cudaMemcpyAsync(d_rowptr, plan->d_rowptr, (size_t)(plan->N + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    if (plan->nnz > 0)
+        EF_CUDA(cudaMemcpyAsync(d_colidx, plan->d_colidx, (size_t)plan->nnz * 4, cudaMemcpyDeviceToDevice, s));
+    return EF_OK;
+}
+
+int ef_plan_topology(const ef_plan* plan, int32_t* d_elem2dof, uint8_t* d_signbits, int32_t* d_dof2nodes,
+                     void* stream)
+{
+    if (!plan) return EF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_elem2dof && plan->T > 0)
+        EF_CUDA(cudaMemcpyAsync(d_elem2dof, plan->d_elem2dof, (size_t)plan->T * plan->nl * 4, cudaMemcpyDeviceToDevice, s));
+    if (d_signbits && plan->T > 0)
+        EF_CUDA(cudaMemcpyAsync(d_signbits, plan->d_signbits, (size_t)plan->T, cudaMemcpyDeviceToDevice, s));
+    if (d_dof2nodes && plan->N > 0)
+        EF_CUDA(cudaMemcpyAsync(d_dof2nodes, plan->d_dof2nodes, (size_t)plan->N * plan->ent * 4,
+                                cudaMemcpyDeviceToDevice, s));
+    return EF_OK;
+}
+
+int ef_assemble_two_pass(const ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval,
+                         double* d_Mval, void* stream)
+{
+    EF_TRY(assemble_checks(plan, d_nodes, d_Kval, d_Mval));
+    return launch_two_pass(plan, d_nodes, d_coeff, d_Kval, d_Mval, (cudaStream_t)stream);
+}
+
+int ef_assemble(const ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
+                void* stream)
+{
+    EF_TRY(assemble_checks(plan, d_nodes, d_Kval, d_Mval));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->use_blocked && plan->fb_nblocks > 0) return launch_fused(plan, d_nodes, d_coeff, d_Kval, d_Mval, s);
+    return launch_pipelined(plan, d_nodes, d_coeff, d_Kval, d_Mval, s);
+}
+
+int ef_assemble_host(ef_plan* plan, const double* h_nodes, const double* h_coeff, double* h_Kval, double* h_Mval,
+                     void* stream)
+{
+    if (!plan) return EF_ERR_ARG;
+    if (plan->T > 0 && (!h_nodes || !h_Kval || !h_Mval)) return EF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = (size_t)(plan->V > 0 ? plan->V : 1) * plan->dim * 8;
+    const size_t cb = (size_t)(plan->T > 0 ? plan->T : 1) * 8;
+    const size_t vb = (size_t)(plan->nnz > 0 ? plan->nnz : 1) * 8;
+    if (!plan->d_stage_nodes) {
+        EF_CUDA(cudaMalloc((void**)&plan->d_stage_nodes, nb));
+        EF_CUDA(cudaMalloc((void**)&plan->d_stage_coeff, cb));
+        EF_CUDA(cudaMalloc((void**)&plan->d_stage_K, vb));
+        EF_CUDA(cudaMalloc((void**)&plan->d_stage_M, vb));
+    }
+    if (plan->V > 0 && h_nodes)
+        EF_CUDA(cudaMemcpyAsync(plan->d_stage_nodes, h_nodes, (size_t)plan->V * plan->dim * 8, cudaMemcpyHostToDevice, s));
+    if (h_coeff && plan->T > 0)
+        EF_CUDA(cudaMemcpyAsync(plan->d_stage_coeff, h_coeff, (size_t)plan->T * 8, cudaMemcpyHostToDevice, s));
+    EF_TRY(ef_assemble(plan, plan->d_stage_nodes, h_coeff ? plan->d_stage_coeff : nullptr, plan->d_stage_K,
+                       plan->d_stage_M, stream));
+    if (plan->nnz > 0) {
+        EF_CUDA(cudaMemcpyAsync(h_Kval, plan->d_stage_K, (size_t)plan->nnz * 8, cudaMemcpyDeviceToHost, s));
+        EF_CUDA(cudaMemcpyAsync(h_Mval, plan->d_stage_M, (size_t)plan->nnz * 8, cudaMemcpyDeviceToHost, s));
+    }
+    return ef_plan_check(plan, stream);
+}
+
+int ef_adjoint(const ef_plan* plan, const double* d_nodes, const double* d_coeff, const double* d_u,
+               const double* d_v, double* d_J, double* d_grad_nodes, double* d_grad_coeff, void* stream)
+{
+    if (!plan || plan->variant != NED3) return EF_ERR_ARG;
+    if (plan->T > 0 && (!d_nodes || !d_u || !d_v)) return EF_ERR_ARG;
+    return launch_adjoint(plan, d_nodes, d_coeff, d_u, d_v, d_J, d_grad_nodes, d_grad_coeff, (cudaStream_t)stream);
+}
+
+int ef_plan_check(ef_plan* plan, void* stream)
+{
+    if (!plan) return EF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = 0;
+    EF_CUDA(cudaMemcpyAsync(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EF_CUDA(cudaStreamSynchronize(s));
+    if (st) EF_CUDA(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
+    if (st & ST_TIMEOUT) return EF_ERR_TIMEOUT;
+    if (st & ST_DEGENERATE) return EF_ERR_DEGENERATE;
+    return EF_OK;
+}
+
+void ef_plan_destroy(ef_plan* plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    destroy_pipeline(plan);
+    free_plan_memory(plan);
+    free(plan);
+}
+
+int rt0_assemble(int dim, const double* d_nodes, int64_t n_nodes, const int32_t* d_elems, int64_t n_elems,
+                 const double* d_coeff, ef_csr* out, void* stream)
+{
+    return one_shot(EF_RT0, dim, d_nodes, n_nodes, d_elems, n_elems, d_coeff, out, stream);
+}
+
+int ned_assemble(int dim, const double* d_nodes, int64_t n_nodes, const int32_t* d_elems, int64_t n_elems,
+                 const double* d_coeff, ef_csr* out, void* stream)
+{
+    return one_shot(EF_NED1, dim, d_nodes, n_nodes, d_elems, n_elems, d_coeff, out, stream);
+}
+
+void ef_csr_free(ef_csr* csr)
+{
+    if (!csr) return;
+    cudaDeviceSynchronize();
+    if (csr->d_rowptr) cudaFree(csr->d_rowptr);
+    if (csr->d_colidx) cudaFree(csr->d_colidx);
+    if (csr->d_K) cudaFree(csr->d_K);
+    if (csr->d_M) cudaFree(csr->d_M);
+    memset(csr, 0, sizeof(*csr));
+}
+
+const char* ef_status_string(int status)
+{
+    switch (status) {
+        case EF_OK: return "ok";
+        case EF_ERR_ARG: return "invalid argument";
+        case EF_ERR_RANGE: return "node id out of range";
+        case EF_ERR_DEGENERATE: return "degenerate element (det B_K = 0)";
+        case EF_ERR_KEY_OVERFLOW: return "face key overflow (n_nodes^3 >= 2^64)";
+        case EF_ERR_OOM: return "device out of memory";
+        case EF_ERR_CUDA: return "CUDA error";
+        case EF_ERR_TIMEOUT: return "bounded device wait timed out";
+        case EF_ERR_SIZE: return "mesh exceeds the 32-bit index limits";
+        default: return "unknown status";
+    }
+}
+
+const char* ef_last_error(void) { return last_error_text(); }
+
+}  // extern "C"

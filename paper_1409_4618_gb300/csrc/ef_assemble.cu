@@ -1,0 +1,227 @@
+// Assembly of K and M values: element kernel + fixed-order segmented sum.
+//
+// Element kernel: one thread per element computes its signed local K and M
+// upper triangles (Sec. 2.4 integrals in closed form, ef_element.cuh) into
+// pair-major scratch, coalesced per pair. This is the FP64-bound part.
+//
+// Sum: one thread per upper nonzero adds its contributions in ascending
+// element order (the order fixed by the plan's stable sort) and writes the
+// value to (r, c) and (c, r). No floating-point atomics.
+//
+// Work order of the sum: the upper nonzeros are grouped by the element chunk
+// that completes them (the chunk of their last contribution) and, inside
+// windows of 256 consecutive nonzeros, by descending contribution count, so
+// that the lanes of a warp run loops of equal length (on this GPU an FP64
+// warp instruction holds the FP64 pipe for its full duration even when lanes
+// are idle) while memory accesses stay local.
+//
+// Pipelined form (ef_assemble): the element kernel runs chunk by chunk on the
+// caller's stream; after each chunk an event lets the plan's second stream
+// sum the nonzeros that chunk completed, while the next chunk computes. The
+// chunk's local matrices are still in L2 when they are read. The caller's
+// stream waits for the last sum before the call's work counts as done.
+#include "ef_assemble.cuh"
+#include "ef_internal.cuh"
+
+namespace ef {
+namespace {
+
+constexpr int TPB = 256;
+
+template <int VAR>
+__global__ void __launch_bounds__(TPB) k_element_local(const int32_t* __restrict__ elems,
+                                                       const double* __restrict__ nodes,
+                                                       const double* __restrict__ coeff, int64_t e0, int64_t e1,
+                                                       int64_t T, double* __restrict__ local, int* status)
+{
+    using E = ElemTraits<VAR>;
+    const int64_t e = e0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (e >= e1) return;
+    double Kq[E::NP], Mq[E::NP];
+    const double sigma = coeff ? __ldg(coeff + e) : 1.0;
+    if (compute_element<VAR>(elems, nodes, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
+#pragma unroll
+    for (int q = 0; q < E::NP; q++) {
+        local[(int64_t)q * T + e] = Kq[q];
+        local[(int64_t)(E::NP + q) * T + e] = Mq[q];
+    }
+}
+
+__global__ void k_work_keys(const uint32_t* seg, const uint32_t* perm, int64_t U, int64_t T, int64_t chunk,
+                            uint64_t* keys, uint32_t* vals, uint32_t* chunk_count)
+{
+    const int64_t u = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (u >= U) return;
+    const uint32_t s0 = seg[u], s1 = seg[u + 1];
+    const uint32_t cnt = s1 - s0;
+    const uint64_t rc = (uint64_t)((perm[s1 - 1] % T) / chunk);
+    keys[u] = (rc << 32) | ((uint64_t)(u >> 8) << 8) | (uint64_t)(255u - (cnt < 255u ? cnt : 255u));
+    vals[u] = (uint32_t)u;
+    atomicAdd(&chunk_count[rc], 1u);
+}
+
+__global__ void __launch_bounds__(TPB) k_scatter(const uint32_t* __restrict__ order, int64_t w0, int64_t w1,
+                                                 const uint32_t* __restrict__ seg, const uint32_t* __restrict__ perm,
+                                                 const uint32_t* __restrict__ pos_up,
+                                                 const uint32_t* __restrict__ pos_lo,
+                                                 const double* __restrict__ localK, const double* __restrict__ localM,
+                                                 double* __restrict__ K, double* __restrict__ M)
+{
+    const int64_t i = w0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= w1) return;
+    const uint32_t u = order[i];
+    const uint32_t s0 = seg[u], s1 = seg[u + 1];
+    uint32_t idx = perm[s0];
+    double k = localK[idx], m = localM[idx];
+    for (uint32_t s = s0 + 1; s < s1; s++) {
+        idx = perm[s];
+        k += localK[idx];
+        m += localM[idx];
+    }
+    uint32_t p = pos_up[u];
+    K[p] = k;
+    M[p] = m;
+    p = pos_lo[u];
+    if (p != 0xffffffffu) {
+        K[p] = k;
+        M[p] = m;
+    }
+}
+
+__global__ void k_count_keys(const uint32_t* seg, const uint32_t* list, int64_t n, uint64_t* keys, uint32_t* vals)
+{
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t u = list[i];
+    const uint32_t cnt = seg[u + 1] - seg[u];
+    keys[i] = ((uint64_t)(i >> 8) << 8) | (uint64_t)(255u - (cnt < 255u ? cnt : 255u));
+    vals[i] = u;
+}
+
+int element_range(const ef_plan* p, const double* nodes, const double* coeff, int64_t e0, int64_t e1,
+                  cudaStream_t s)
+{
+    if (e1 <= e0) return EF_OK;
+    const unsigned grid = (unsigned)((e1 - e0 + TPB - 1) / TPB);
+    switch (p->variant) {
+        case RT2: k_element_local<RT2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
+        case NED2: k_element_local<NED2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT3: k_element_local<RT3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
+        default: k_element_local<NED3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
+    }
+    EF_CUDA(cudaGetLastError());
+    return EF_OK;
+}
+
+int scatter_range(const ef_plan* p, int64_t w0, int64_t w1, double* K, double* M, cudaStream_t s)
+{
+    if (w1 <= w0) return EF_OK;
+    const unsigned grid = (unsigned)((w1 - w0 + TPB - 1) / TPB);
+    const double* lK = p->d_local;
+    const double* lM = p->d_local + (int64_t)p->np * p->T;
+    k_scatter<<<grid, TPB, 0, s>>>(p->d_uorder, w0, w1, p->d_seg, p->d_perm, p->d_pos_up, p->d_pos_lo, lK, lM, K, M);
+    EF_CUDA(cudaGetLastError());
+    return EF_OK;
+}
+
+}  // namespace
+
+// Reorder `list` (upper nonzero ids) inside windows of 256 entries by
+// descending contribution count (stable). keys / vals: n entries of scratch.
+int order_by_count(const uint32_t* seg, uint32_t* list, int64_t n, uint64_t* keys, uint32_t* vals, void* tmp,
+                   cudaStream_t s)
+{
+    if (n <= 1) return EF_OK;
+    k_count_keys<<<(unsigned)((n + TPB - 1) / TPB), TPB, 0, s>>>(seg, list, n, keys, vals);
+    EF_CUDA(cudaGetLastError());
+    EF_TRY(radix_sort_pairs(keys, vals, n, bits_for(((uint64_t)(n >> 8) << 8) | 255u), tmp, s));
+    EF_CUDA(cudaMemcpyAsync(list, vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    return EF_OK;
+}
+
+int build_scatter_order(ef_plan* p, cudaStream_t s)
+{
+    p->pc_chunks = 0;
+    if (p->U == 0) return EF_OK;
+    const int64_t U = p->U, T = p->T;
+    // chunks of at least 64K elements, at most EF_MAX_CHUNKS of them
+    int64_t chunk = (T + EF_MAX_CHUNKS - 1) / EF_MAX_CHUNKS;
+    if (chunk < 65536) chunk = 65536;
+    chunk = (chunk + TPB - 1) / TPB * TPB;
+    const int nc = (int)((T + chunk - 1) / chunk);
+    uint64_t* keys = nullptr;
+    uint32_t* cnt = nullptr;
+    void* tmp = nullptr;
+    int st = EF_OK;
+    if (cudaMalloc((void**)&p->d_uorder, U * 4) != cudaSuccess || cudaMalloc((void**)&keys, U * 8) != cudaSuccess ||
+        cudaMalloc((void**)&cnt, EF_MAX_CHUNKS * 4) != cudaSuccess ||
+        cudaMalloc(&tmp, radix_tmp_bytes(U)) != cudaSuccess)
+        st = EF_ERR_OOM;
+    uint32_t hc[EF_MAX_CHUNKS] = {0};
+    if (st == EF_OK) {
+        cudaMemsetAsync(cnt, 0, EF_MAX_CHUNKS * 4, s);
+        k_work_keys<<<(unsigned)((U + TPB - 1) / TPB), TPB, 0, s>>>(p->d_seg, p->d_perm, U, T, chunk, keys, p->d_uorder, cnt);
+        st = radix_sort_pairs(keys, p->d_uorder, U, bits_for(((uint64_t)(nc - 1) << 32) | 0xffffffffull), tmp, s);
+        if (st == EF_OK) cudaMemcpyAsync(hc, cnt, EF_MAX_CHUNKS * 4, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (st == EF_OK && e != cudaSuccess) {
+            set_last_error("build_scatter_order", e);
+            st = EF_ERR_CUDA;
+        }
+    }
+    cudaFree(keys);
+    cudaFree(cnt);
+    cudaFree(tmp);
+    if (st != EF_OK) return st;
+    p->pc_chunks = nc;
+    p->pc_chunk = chunk;
+    p->pc_woff[0] = 0;
+    for (int c = 0; c < nc; c++) p->pc_woff[c + 1] = p->pc_woff[c] + hc[c];
+    if (nc > 1) {
+        int lo, hi;
+        EF_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        EF_CUDA(cudaStreamCreateWithPriority(&p->pc_aux, cudaStreamNonBlocking, hi));
+        for (int c = 0; c <= nc; c++) EF_CUDA(cudaEventCreateWithFlags(&p->pc_ev[c], cudaEventDisableTiming));
+    }
+    return EF_OK;
+}
+
+int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
+                    cudaStream_t s)
+{
+    if (p->T == 0) return EF_OK;
+    EF_TRY(element_range(p, nodes, coeff, 0, p->T, s));
+    return scatter_range(p, 0, p->U, K, M, s);
+}
+
+int launch_pipelined(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
+                     cudaStream_t s)
+{
+    if (p->T == 0) return EF_OK;
+    const int nc = p->pc_chunks;
+    if (nc <= 1) return launch_two_pass(p, nodes, coeff, K, M, s);
+    for (int c = 0; c < nc; c++) {
+        const int64_t e0 = (int64_t)c * p->pc_chunk;
+        const int64_t e1 = e0 + p->pc_chunk < p->T ? e0 + p->pc_chunk : p->T;
+        EF_TRY(element_range(p, nodes, coeff, e0, e1, s));
+        EF_CUDA(cudaEventRecord(p->pc_ev[c], s));
+        EF_CUDA(cudaStreamWaitEvent(p->pc_aux, p->pc_ev[c], 0));
+        EF_TRY(scatter_range(p, (int64_t)p->pc_woff[c], (int64_t)p->pc_woff[c + 1], K, M, p->pc_aux));
+    }
+    EF_CUDA(cudaEventRecord(p->pc_ev[nc], p->pc_aux));
+    EF_CUDA(cudaStreamWaitEvent(s, p->pc_ev[nc], 0));
+    return EF_OK;
+}
+
+void destroy_pipeline(ef_plan* p)
+{
+    if (p->pc_chunks > 1) {
+        for (int c = 0; c <= p->pc_chunks; c++)
+            if (p->pc_ev[c]) cudaEventDestroy(p->pc_ev[c]);
+        if (p->pc_aux) cudaStreamDestroy(p->pc_aux);
+    }
+    p->pc_aux = nullptr;
+    p->pc_chunks = 0;
+}
+
+}  // namespace ef

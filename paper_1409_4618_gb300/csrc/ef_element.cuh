@@ -1,0 +1,270 @@
+// Per-element local matrices in closed form (FP64), shared by the element
+// kernels of the two-pass and fused paths.
+//
+// Each function returns the upper triangle (k <= l, row-major) of the
+// signed local K and M of one element, times its coefficient sigma:
+//
+//   RT0 (Eq. RT0local2 with Piola map RT0piola): with eta_k = x - p_opp(k)
+//   (Sec. 2.1, the opposite vertex of DOF k), B eta_k(xhat) = x - P_a, so
+//     M_kl = s_k s_l sigma / det^2 * int_K (x - P_a).(x - P_b) dx,
+//     K_kl = s_k s_l sigma (div eta)^2 |Khat| / |det|
+//   and int_K lambda_i lambda_j = |K| (1 + delta_ij) / ((d+1)(d+2)) gives,
+//   with y_i = P_i - P_0, S = sum_i y_i, H = Gram(y_1..y_d):
+//     int_K (x-P_a).(x-P_b) = |K|/((d+1)(d+2)) [S.S + tr H - (d+2) S.(y_a+y_b) + (d+1)(d+2) y_a.y_b].
+//   Nedelec (Sec. 2.4, Ned0piola1-3): B^-T eta_k is the Whitney form
+//   lambda_t grad lambda_h - lambda_h grad lambda_t of its edge (t -> h), so
+//     M_(ab)(cd) = sigma |K|/((d+1)(d+2)) [(1+d_ac)G_bd - (1+d_ad)G_bc - (1+d_bc)G_ad + (1+d_bd)G_ac],
+//   G_ij = grad lambda_i . grad lambda_j = adj(H)_ij / det^2 (rows 1..d of
+//   B^-1 scaled by det), grad lambda_0 = -sum_i grad lambda_i. In 3D,
+//   B curl eta_k = 2 w_k with w = (e3-e2, e1-e3, e2-e1, e3, e1, e2), e_i the
+//   columns of B, so K_kl = (2 sigma / (3 |det|)) w_k . w_l, a combination of
+//   the entries of H = B^T B. In 2D every curl is 2/det, K_kl = 2 sigma/|det|.
+//
+// Signs are applied by flipping the IEEE sign bit (integer XOR), so they cost
+// no floating-point work. |det B| enters only through r = 1/|det B|, with det B
+// from the triple product (accurate to cond(B) eps, also on nearly flat
+// elements).
+#pragma once
+
+#include <stdint.h>
+
+namespace ef {
+
+// local DOF entities (Fig. 1), 0-based
+__device__ __constant__ const int8_t kEdge2[3][2] = {{1, 2}, {2, 0}, {0, 1}};
+__device__ __constant__ const int8_t kEdge3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {2, 3}, {3, 1}};
+__device__ __constant__ const int8_t kFace3[4][4] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 3, 1}, {1, 2, 3, 0}};
+
+__device__ __forceinline__ double flip_if(double x, uint32_t f)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(f & 1u) << 63));
+}
+
+// Orientation sign bits (bit k set iff s_k = -1), from global node ids only.
+// Edges: s = +1 iff id(tail) > id(head). Faces: s = -parity of the
+// permutation (face nodes by ascending id, opposite node).
+template <int VAR>
+__device__ __forceinline__ uint32_t sign_bits(const int32_t* g)
+{
+    uint32_t bits = 0;
+    if (VAR == 1) {  // RT3: faces
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int a = kFace3[k][0], b = kFace3[k][1], c = kFace3[k][2];
+            // inversions among the three face nodes when sorted by id, relative to (a,b,c)
+            int inv = (g[a] > g[b]) + (g[a] > g[c]) + (g[b] > g[c]);
+            // positions: sorted face nodes keep the relative order of (a,b,c) up to `inv`
+            // inversions; the opposite node 3-k comes last. Inversions of the full
+            // permutation = inv + (number of face positions greater than the opposite one).
+            int opp = 3 - k;
+            int tail = (a > opp) + (b > opp) + (c > opp);
+            int parity_even = ((inv + tail) & 1) == 0;
+            bits |= (uint32_t)parity_even << k;   // s = -1 for even permutations
+        }
+    } else if (VAR == 3) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) bits |= (uint32_t)(g[kEdge3[k][0]] < g[kEdge3[k][1]]) << k;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++) bits |= (uint32_t)(g[kEdge2[k][0]] < g[kEdge2[k][1]]) << k;
+    }
+    return bits;
+}
+
+// det H <= 0 (or NaN) marks a degenerate element; tested on the bit pattern.
+__device__ __forceinline__ bool not_positive(double x)
+{
+    long long b = __double_as_longlong(x);
+    return b <= 0 || (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+}
+
+// ---- 3D Nedelec: 21 + 21 upper entries ---------------------------------------
+__device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma, uint32_t neg, double (&Kq)[21],
+                                           double (&Mq)[21])
+{
+    const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
+    const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
+    const double e3x = p[3][0] - p[0][0], e3y = p[3][1] - p[0][1], e3z = p[3][2] - p[0][2];
+    const double H11 = fma(e1z, e1z, fma(e1y, e1y, e1x * e1x));
+    const double H22 = fma(e2z, e2z, fma(e2y, e2y, e2x * e2x));
+    const double H33 = fma(e3z, e3z, fma(e3y, e3y, e3x * e3x));
+    const double H12 = fma(e1z, e2z, fma(e1y, e2y, e1x * e2x));
+    const double H13 = fma(e1z, e3z, fma(e1y, e3y, e1x * e3x));
+    const double H23 = fma(e2z, e3z, fma(e2y, e3y, e2x * e3x));
+    // adj(H) = det(B)^2 * Gram(grad lambda_1..3)
+    const double A11 = fma(H22, H33, -(H23 * H23));
+    const double A22 = fma(H11, H33, -(H13 * H13));
+    const double A33 = fma(H11, H22, -(H12 * H12));
+    const double A12 = fma(H13, H23, -(H12 * H33));
+    const double A13 = fma(H12, H23, -(H13 * H22));
+    const double A23 = fma(H12, H13, -(H11 * H23));
+    // det B by the triple product e1 . (e2 x e3): its error grows like cond(B),
+    // where det(H) = det(B)^2 from the Gram matrix would grow like cond(B)^2
+    const double cx = fma(e2y, e3z, -(e2z * e3y)), cy = fma(e2z, e3x, -(e2x * e3z)), cz = fma(e2x, e3y, -(e2y * e3x));
+    const double adet = fabs(fma(e1z, cz, fma(e1y, cy, e1x * cx)));
+    const bool bad = not_positive(adet);
+    const double r = 1.0 / adet;
+    const double sr = sigma * r;
+
+    // K_kl = (2 sigma / (3|det|)) w_k . w_l
+    const double cK = sr * (2.0 / 3.0);
+    const double h11 = cK * H11, h22 = cK * H22, h33 = cK * H33, h12 = cK * H12, h13 = cK * H13, h23 = cK * H23;
+    const double k03 = h33 - h23, k04 = h13 - h12, k05 = h23 - h22;
+    const double k13 = h13 - h33, k14 = h11 - h13, k15 = h12 - h23;
+    const double k23 = h23 - h13, k24 = h12 - h11, k25 = h22 - h12;
+    const double k00 = k03 - k05, k11 = k14 - k13, k22 = k25 - k24;
+    const double k01 = k04 - k03, k02 = k05 - k04, k12 = k15 - k14;
+    // M: Whitney-form combinations of g = sigma/(120|det|) adj(H), node 0 row from sum-zero
+    const double cM = sr * (1.0 / 120.0);
+    const double g11 = cM * A11, g22 = cM * A22, g33 = cM * A33, g12 = cM * A12, g13 = cM * A13, g23 = cM * A23;
+    const double g01 = -(g11 + g12 + g13), g02 = -(g12 + g22 + g23), g03 = -(g13 + g23 + g33);
+    const double g00 = -(g01 + g02 + g03);
+    double d;
+
+    // order: (0,0)..(0,5), (1,1)..(1,5), (2,2)..(2,5), (3,3)..(3,5), (4,4),(4,5), (5,5)
+    Kq[0] = k00; Kq[1] = k01; Kq[2] = k02; Kq[3] = k03; Kq[4] = k04; Kq[5] = k05;
+    Kq[6] = k11; Kq[7] = k12; Kq[8] = k13; Kq[9] = k14; Kq[10] = k15;
+    Kq[11] = k22; Kq[12] = k23; Kq[13] = k24; Kq[14] = k25;
+    Kq[15] = h33; Kq[16] = h13; Kq[17] = h23;
+    Kq[18] = h11; Kq[19] = h12;
+    Kq[20] = h22;
+
+    d = g00 + g11 - g01; Mq[0] = d + d;
+    Mq[1] = fma(2.0, g12, g00 - g01 - g02);
+    Mq[2] = fma(2.0, g13, g00 - g01 - g03);
+    Mq[3] = fma(-2.0, g02, g12 - g11 + g01);
+    Mq[4] = (g13 - g12) - (g03 - g02);
+    Mq[5] = fma(2.0, g03, g11 - g13 - g01);
+    d = g00 + g22 - g02; Mq[6] = d + d;
+    Mq[7] = fma(2.0, g23, g00 - g02 - g03);
+    Mq[8] = fma(2.0, g01, g22 - g12 - g02);
+    Mq[9] = fma(-2.0, g03, g23 - g22 + g02);
+    Mq[10] = (g12 - g23) - (g01 - g03);
+    d = g00 + g33 - g03; Mq[11] = d + d;
+    Mq[12] = (g23 - g13) - (g02 - g01);
+    Mq[13] = fma(2.0, g02, g33 - g23 - g03);
+    Mq[14] = fma(-2.0, g01, g13 - g33 + g03);
+    d = g11 + g22 - g12; Mq[15] = d + d;
+    Mq[16] = fma(-2.0, g13, g23 - g22 + g12);
+    Mq[17] = fma(-2.0, g23, g12 - g11 + g13);
+    d = g22 + g33 - g23; Mq[18] = d + d;
+    Mq[19] = fma(-2.0, g12, g13 - g33 + g23);
+    d = g33 + g11 - g13; Mq[20] = d + d;
+
+    // signs s_k s_l on the off-diagonal pairs
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+#pragma unroll
+        for (int l = k; l < 6; l++, q++) {
+            uint32_t f = (neg >> k) ^ (neg >> l);
+            Kq[q] = flip_if(Kq[q], f);
+            Mq[q] = flip_if(Mq[q], f);
+        }
+    return bad;
+}
+
+// ---- 3D RT0: 10 + 10 upper entries (DOF k <-> opposite vertex 3-k) ---------
+__device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigma, uint32_t neg, double (&Kq)[10],
+                                          double (&Mq)[10])
+{
+    const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
+    const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
+    const double e3x = p[3][0] - p[0][0], e3y = p[3][1] - p[0][1], e3z = p[3][2] - p[0][2];
+    const double H11 = fma(e1z, e1z, fma(e1y, e1y, e1x * e1x));
+    const double H22 = fma(e2z, e2z, fma(e2y, e2y, e2x * e2x));
+    const double H33 = fma(e3z, e3z, fma(e3y, e3y, e3x * e3x));
+    const double H12 = fma(e1z, e2z, fma(e1y, e2y, e1x * e2x));
+    const double H13 = fma(e1z, e3z, fma(e1y, e3y, e1x * e3x));
+    const double H23 = fma(e2z, e3z, fma(e2y, e3y, e2x * e3x));
+    const double cx = fma(e2y, e3z, -(e2z * e3y)), cy = fma(e2z, e3x, -(e2x * e3z)), cz = fma(e2x, e3y, -(e2y * e3x));
+    const double det = fma(e1z, cz, fma(e1y, cy, e1x * cx));
+    const bool bad = not_positive(fabs(det));
+    const double r = 1.0 / fabs(det);
+    const double sr = sigma * r;
+    // M: sigma/(120|det|) [c0 - 5 (S.y_a + S.y_b) + 20 y_a.y_b]
+    const double r1 = H11 + H12 + H13, r2 = H12 + H22 + H23, r3 = H13 + H23 + H33;
+    const double c0 = (r1 + r2 + r3) + (H11 + H22 + H33);
+    const double cM = sr * (1.0 / 120.0);
+    const double m5 = -5.0 * cM, m20 = 20.0 * cM;
+    const double c0s = c0 * cM;
+    const double q1 = r1 * m5, q2 = r2 * m5, q3 = r3 * m5;
+    const double t1 = c0s + q1, t2 = c0s + q2, t3 = c0s + q3;
+    // DOF k <-> opposite vertex a = 3 - k; vertex 0 has y_0 = 0
+    // (0,0):a=3  (0,1):3,2  (0,2):3,1  (0,3):3,0  (1,1):2  (1,2):2,1  (1,3):2,0  (2,2):1  (2,3):1,0  (3,3):0
+    Mq[0] = fma(m20, H33, t3 + q3);
+    Mq[1] = fma(m20, H23, t3 + q2);
+    Mq[2] = fma(m20, H13, t3 + q1);
+    Mq[3] = t3;
+    Mq[4] = fma(m20, H22, t2 + q2);
+    Mq[5] = fma(m20, H12, t2 + q1);
+    Mq[6] = t2;
+    Mq[7] = fma(m20, H11, t1 + q1);
+    Mq[8] = t1;
+    Mq[9] = c0s;
+    const double kv = sr * 1.5;   // (div eta)^2 |Khat| = 9/6
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int l = k; l < 4; l++, q++) {
+            uint32_t f = (neg >> k) ^ (neg >> l);
+            Kq[q] = flip_if(kv, f);
+            Mq[q] = flip_if(Mq[q], f);
+        }
+    return bad;
+}
+
+// ---- 2D RT0 (VAR 0) and 2D Nedelec (VAR 2): 6 + 6 upper entries ------------
+template <int VAR>
+__device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigma, uint32_t neg, double (&Kq)[6],
+                                          double (&Mq)[6])
+{
+    const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1];
+    const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1];
+    const double H11 = fma(e1y, e1y, e1x * e1x), H22 = fma(e2y, e2y, e2x * e2x), H12 = fma(e1y, e2y, e1x * e2x);
+    const double det = fma(e1x, e2y, -(e1y * e2x));
+    const bool bad = not_positive(fabs(det));
+    const double r = 1.0 / fabs(det);
+    const double sr = sigma * r;
+    const double cM = sr * (1.0 / 24.0);
+    if (VAR == 0) {
+        // RT0: sigma/(24|det|) [c0 - 4 (S.y_a + S.y_b) + 12 y_a.y_b], DOF k <-> vertex k
+        const double r1 = H11 + H12, r2 = H12 + H22;
+        const double c0 = (r1 + r2) + (H11 + H22);
+        const double m4 = -4.0 * cM, m12 = 12.0 * cM;
+        const double c0s = c0 * cM, q1 = r1 * m4, q2 = r2 * m4;
+        const double t1 = c0s + q1, t2 = c0s + q2;
+        Mq[0] = c0s;                          // (0,0)
+        Mq[1] = t1;                           // (0,1)
+        Mq[2] = t2;                           // (0,2)
+        Mq[3] = fma(m12, H11, t1 + q1);       // (1,1)
+        Mq[4] = fma(m12, H12, t1 + q2);       // (1,2)
+        Mq[5] = fma(m12, H22, t2 + q2);       // (2,2)
+    } else {
+        // Nedelec: Whitney forms on edges (1,2), (2,0), (0,1); g = sigma/(24|det|) adj(H)
+        const double g11 = cM * H22, g22 = cM * H11, g12 = -(cM * H12);
+        const double g01 = -(g11 + g12), g02 = -(g12 + g22);
+        const double g00 = -(g01 + g02);
+        double d;
+        d = g11 + g22 - g12; Mq[0] = d + d;
+        Mq[1] = fma(-2.0, g01, g02 - g22 + g12);
+        Mq[2] = fma(-2.0, g02, g12 - g11 + g01);
+        d = g22 + g00 - g02; Mq[3] = d + d;
+        Mq[4] = fma(-2.0, g12, g01 - g00 + g02);
+        d = g00 + g11 - g01; Mq[5] = d + d;
+    }
+    const double kv = sr * 2.0;   // (div eta)^2 |Khat| = 4/2 (RT); curl^2 |Khat| = 4/2 (Ned)
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int l = k; l < 3; l++, q++) {
+            uint32_t f = (neg >> k) ^ (neg >> l);
+            Kq[q] = flip_if(kv, f);
+            Mq[q] = flip_if(Mq[q], f);
+        }
+    return bad;
+}
+
+}  // namespace ef

@@ -1,0 +1,146 @@
+// Internal declarations of libedgefem (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/edgefem.h"
+
+namespace ef {
+
+// Element kinds handled by one plan.
+enum Variant { RT2 = 0, RT3 = 1, NED2 = 2, NED3 = 3 };
+
+inline int variant_of(int kind, int dim)
+{
+    if (kind == EF_RT0) return dim == 2 ? RT2 : RT3;
+    return dim == 2 ? NED2 : NED3;
+}
+// local DOFs per element: edges (3 or 6) or faces (4)
+inline int nloc_of(int v) { return v == RT3 ? 4 : (v == NED3 ? 6 : 3); }
+// nodes of the mesh entity carrying a DOF: 2 (edge) or 3 (face)
+inline int ent_nodes_of(int v) { return v == RT3 ? 3 : 2; }
+// upper-triangle pairs (k <= l) of a local matrix
+inline int npair_of(int v)
+{
+    int n = nloc_of(v);
+    return n * (n + 1) / 2;
+}
+
+// Device status bits (plan->d_status).
+enum : int { ST_DEGENERATE = 1, ST_RANGE = 2, ST_REPEAT = 4, ST_TIMEOUT = 8 };
+
+// Error helpers ------------------------------------------------------------
+void set_last_error(const char* where, cudaError_t err);
+#define EF_CUDA(call)                                    \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) {                         \
+            ::ef::set_last_error(#call, e_);             \
+            return e_ == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA; \
+        }                                                \
+    } while (0)
+#define EF_TRY(expr)          \
+    do {                      \
+        int s_ = (expr);      \
+        if (s_ != EF_OK) return s_; \
+    } while (0)
+
+// Exclusive prefix sums -------------------------------------------------------
+// out[i] = sum_{j<i} in[j] for i < n; out[n] = total when write_total.
+// tmp: scan_tmp_bytes(n) bytes of device scratch.
+size_t scan_tmp_bytes(int64_t n);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, bool write_total, void* tmp, cudaStream_t s);
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, bool write_total, void* tmp, cudaStream_t s);
+
+// Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low `bits`
+// bits of the keys. Result ends in keys/vals. Scratch: radix_tmp_bytes(n).
+size_t radix_tmp_bytes(int64_t n);
+int radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int bits, void* tmp, cudaStream_t s);
+
+inline int bits_for(uint64_t max_value)
+{
+    int b = 0;
+    while (b < 64 && (max_value >> b) != 0) b++;
+    return b;
+}
+
+}  // namespace ef
+
+#define EF_MAX_CHUNKS 16
+
+// The plan object behind the opaque C handle.
+struct ef_plan {
+    int kind, dim, variant;
+    int nv;     // nodes per element
+    int nl;     // local DOFs
+    int np;     // upper pairs per element
+    int ent;    // nodes per DOF entity
+    int64_t V, T, N, nnz, U;  // nodes, elements, DOFs, CSR nonzeros, upper nonzeros
+
+    int32_t* d_elems;     // T x nv (plan copy)
+    int32_t* d_elem2dof;  // T x nl
+    uint8_t* d_signbits;  // T
+    int32_t* d_dof2nodes; // N x ent
+    int64_t* d_rowptr;    // N + 1
+    int32_t* d_colidx;    // nnz
+    uint32_t* d_seg;      // U + 1: contribution range of each upper nonzero
+    uint32_t* d_perm;     // T * np: local-matrix index (pair * T + elem) of each contribution, segment order
+    uint32_t* d_pos_up;   // U: CSR position of (r, c), r <= c
+    uint32_t* d_pos_lo;   // U: CSR position of (c, r), or 0xffffffff on the diagonal
+    uint32_t* d_uorder;   // U: work order of the sum (completing chunk, then count inside 256-windows)
+    double* d_local;      // 2 * np * T: scratch for the two-pass path (K pairs then M pairs)
+    int* d_status;        // device status word
+
+    // fused path (blocks of fb_block consecutive elements): see ef_fused.cu
+    int fb_block;             // elements per block (0: no fused schedule)
+    int64_t fb_nblocks;
+    int64_t fb_nslots;
+    uint32_t* d_fb_slot_off;  // nblocks + 1: slot range of each block
+    uint32_t* d_fb_sinfo;     // per slot: start | count << 16 | partial << 31
+    uint32_t* d_fb_posA;      // per slot: CSR position of (r,c), or first global list position if partial
+    uint32_t* d_fb_posB;      // per slot: CSR position of (c,r), or 0xffffffff
+    uint16_t* d_fb_cidx;      // per contribution, block-major: pair * block + element in block
+    uint32_t* d_px_uid;       // upper nonzeros split across blocks (summed by the fix-up)
+    int64_t n_px;
+    int64_t n_partial;        // raw contributions of the split nonzeros
+
+    // adjoint (3D Nedelec): node -> (element, vertex) incidence in element order, scratch
+    uint32_t* d_node_off;    // V + 1
+    uint32_t* d_node_inc;    // T * 4: element * 4 + vertex, grouped by node
+    double* d_adj_part;      // T * 4 * 3: per (element, vertex) gradient
+    double* d_adj_jpart;     // per-CTA partial energies
+
+    // pipelined two-pass: element chunks on the caller's stream, sums on pc_aux
+    int pc_chunks;                       // number of element chunks (<= 1: not pipelined)
+    int64_t pc_chunk;                    // elements per chunk
+    uint32_t pc_woff[EF_MAX_CHUNKS + 1]; // work-list range of the sums each chunk completes
+    cudaStream_t pc_aux;
+    cudaEvent_t pc_ev[EF_MAX_CHUNKS + 1];
+    int use_blocked;                     // ef_assemble runs the element-block kernel (ef_plan_set_block)
+
+    // host staging for ef_assemble_host
+    double *d_stage_nodes, *d_stage_coeff, *d_stage_K, *d_stage_M;
+};
+
+namespace ef {
+const char* last_error_text();
+int validate_elems(ef_plan* p, cudaStream_t s);
+int build_topology(ef_plan* p, cudaStream_t s);
+int build_pattern(ef_plan* p, cudaStream_t s);
+int build_fused(ef_plan* p, cudaStream_t s);
+int build_scatter_order(ef_plan* p, cudaStream_t s);
+// Order a list of upper nonzeros by descending contribution count (stable), in place.
+int order_by_count(const uint32_t* seg, uint32_t* list, int64_t n, uint64_t* keys, uint32_t* vals, void* tmp,
+                   cudaStream_t s);
+int build_fused_block(ef_plan* p, int BE, cudaStream_t s);
+bool fused_block_supported(int BE);
+int build_adjoint(ef_plan* p, cudaStream_t s);
+int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);
+int launch_pipelined(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
+                     cudaStream_t s);
+void destroy_pipeline(ef_plan* p);
+int launch_fused(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);
+int launch_adjoint(const ef_plan* p, const double* nodes, const double* coeff, const double* u, const double* v,
+                   double* J, double* gx, double* gs, cudaStream_t s);
+}  // namespace ef

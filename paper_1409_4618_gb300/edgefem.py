@@ -1,0 +1,316 @@
+"""Python binding of libedgefem.so (include/edgefem.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch only provides device
+memory and the current stream. There is no CPU path: if the library is not
+built or no CUDA device is present, the calls raise.
+
+Names follow the C ABI: ``ef_plan_create``, ``ef_assemble``, ...; ``Plan``
+bundles a plan handle with its sizes, and ``rt0_assemble`` / ``ned_assemble``
+are the one-shot calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+EF_RT0 = 1
+EF_NED1 = 2
+
+EF_OK = 0
+EF_ERR_ARG = -1
+EF_ERR_RANGE = -2
+EF_ERR_DEGENERATE = -3
+EF_ERR_KEY_OVERFLOW = -4
+EF_ERR_OOM = -5
+EF_ERR_CUDA = -6
+EF_ERR_TIMEOUT = -7
+EF_ERR_SIZE = -8
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EdgeFemError(RuntimeError):
+    def __init__(self, code: int, text: str, detail: str = ""):
+        msg = f"edgefem status {code}: {text}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+        self.code = code
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n_dofs", C.c_int64), ("nnz", C.c_int64), ("n_upper", C.c_int64), ("n_contrib", C.c_int64),
+                ("assemble_launches", C.c_int32), ("fused_block", C.c_int32), ("fused_blocks", C.c_int64),
+                ("fused_partial", C.c_int64), ("pipeline_chunks", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _CSR(C.Structure):
+    _fields_ = [("n_dofs", C.c_int64), ("nnz", C.c_int64), ("d_rowptr", C.c_void_p), ("d_colidx", C.c_void_p),
+                ("d_K", C.c_void_p), ("d_M", C.c_void_p)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libedgefem.so (building it first if it is missing or stale and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libedgefem.so not found at {_build.LIB}; run python -m paper_1409_4618_gb300.build")
+        lib = C.CDLL(_build.LIB)
+        P, I64, I = C.c_void_p, C.c_int64, C.c_int
+        sig = {
+            "ef_plan_create": ([I, I, I64, I64, P, P, C.POINTER(P)], I),
+            "ef_plan_sizes": ([P, C.POINTER(I64), C.POINTER(I64)], I),
+            "ef_plan_pattern": ([P, P, P, P], I),
+            "ef_plan_info": ([P, C.POINTER(PlanInfo)], I),
+            "ef_plan_set_block": ([P, I, P], I),
+            "ef_plan_topology": ([P, P, P, P, P], I),
+            "ef_assemble": ([P, P, P, P, P, P], I),
+            "ef_assemble_two_pass": ([P, P, P, P, P, P], I),
+            "ef_assemble_host": ([P, P, P, P, P, P], I),
+            "ef_plan_check": ([P, P], I),
+            "ef_adjoint": ([P, P, P, P, P, P, P, P, P], I),
+            "ef_plan_destroy": ([P], None),
+            "rt0_assemble": ([I, P, I64, P, I64, P, C.POINTER(_CSR), P], I),
+            "ned_assemble": ([I, P, I64, P, I64, P, C.POINTER(_CSR), P], I),
+            "ef_csr_free": ([C.POINTER(_CSR)], None),
+            "ef_status_string": ([I], C.c_char_p),
+            "ef_last_error": ([], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != EF_OK:
+        lib = load()
+        raise EdgeFemError(st, lib.ef_status_string(st).decode(), lib.ef_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host(t, dtype, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CPU tensor of dtype {dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def ef_plan_create(kind: int, dim: int, n_nodes: int, elems: torch.Tensor, stream=None) -> C.c_void_p:
+    lib = load()
+    h = C.c_void_p()
+    _check(lib.ef_plan_create(kind, dim, int(n_nodes), int(elems.shape[0]), _dev(elems, torch.int32, "elems"),
+                              _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def ef_plan_sizes(plan) -> tuple[int, int]:
+    n, z = C.c_int64(), C.c_int64()
+    _check(load().ef_plan_sizes(plan, C.byref(n), C.byref(z)))
+    return n.value, z.value
+
+
+def ef_plan_info(plan) -> dict:
+    info = PlanInfo()
+    _check(load().ef_plan_info(plan, C.byref(info)))
+    return info.as_dict()
+
+
+def ef_plan_set_block(plan, block: int, stream=None):
+    _check(load().ef_plan_set_block(plan, int(block), _stream_ptr(stream)))
+
+
+def ef_plan_pattern(plan, rowptr: torch.Tensor, colidx: torch.Tensor, stream=None):
+    _check(load().ef_plan_pattern(plan, _dev(rowptr, torch.int64, "rowptr"), _dev(colidx, torch.int32, "colidx"),
+                                  _stream_ptr(stream)))
+
+
+def ef_plan_topology(plan, elem2dof=None, signbits=None, dof2nodes=None, stream=None):
+    _check(load().ef_plan_topology(plan, _dev(elem2dof, torch.int32, "elem2dof"), _dev(signbits, torch.uint8, "signbits"),
+                                   _dev(dof2nodes, torch.int32, "dof2nodes"), _stream_ptr(stream)))
+
+
+def ef_assemble(plan, nodes, coeff, K, M, stream=None):
+    _check(load().ef_assemble(plan, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
+                              _dev(K, torch.float64, "K"), _dev(M, torch.float64, "M"), _stream_ptr(stream)))
+
+
+def ef_assemble_two_pass(plan, nodes, coeff, K, M, stream=None):
+    _check(load().ef_assemble_two_pass(plan, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
+                                       _dev(K, torch.float64, "K"), _dev(M, torch.float64, "M"), _stream_ptr(stream)))
+
+
+def ef_assemble_host(plan, nodes, coeff, K, M, stream=None):
+    _check(load().ef_assemble_host(plan, _host(nodes, torch.float64, "nodes"), _host(coeff, torch.float64, "coeff"),
+                                   _host(K, torch.float64, "K"), _host(M, torch.float64, "M"), _stream_ptr(stream)))
+
+
+def ef_adjoint(plan, nodes, coeff, u, v, J=None, grad_nodes=None, grad_coeff=None, stream=None):
+    _check(load().ef_adjoint(plan, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
+                             _dev(u, torch.float64, "u"), _dev(v, torch.float64, "v"), _dev(J, torch.float64, "J"),
+                             _dev(grad_nodes, torch.float64, "grad_nodes"), _dev(grad_coeff, torch.float64, "grad_coeff"),
+                             _stream_ptr(stream)))
+
+
+def ef_plan_check(plan, stream=None):
+    _check(load().ef_plan_check(plan, _stream_ptr(stream)))
+
+
+def ef_plan_destroy(plan):
+    load().ef_plan_destroy(plan)
+
+
+class _DevArray:
+    """Exposes a raw device pointer through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2}
+
+
+def _one_shot(fn, dim, nodes, elems, coeff, stream):
+    lib = load()
+    csr = _CSR()
+    _check(getattr(lib, fn)(dim, _dev(nodes, torch.float64, "nodes"), int(nodes.shape[0]),
+                            _dev(elems, torch.int32, "elems"), int(elems.shape[0]),
+                            _dev(coeff, torch.float64, "coeff"), C.byref(csr), _stream_ptr(stream)))
+    try:
+        out = {}
+        for key, ptr, n, ts, dt in (("rowptr", csr.d_rowptr, csr.n_dofs + 1, "<i8", torch.int64),
+                                    ("colidx", csr.d_colidx, csr.nnz, "<i4", torch.int32),
+                                    ("K", csr.d_K, csr.nnz, "<f8", torch.float64),
+                                    ("M", csr.d_M, csr.nnz, "<f8", torch.float64)):
+            if n > 0:
+                out[key] = torch.as_tensor(_DevArray(ptr, n, ts), device=nodes.device).clone()
+            else:
+                out[key] = torch.zeros(0, dtype=dt, device=nodes.device)
+        torch.cuda.current_stream().synchronize()
+        return out
+    finally:
+        lib.ef_csr_free(C.byref(csr))
+
+
+def rt0_assemble(dim: int, nodes: torch.Tensor, elems: torch.Tensor, coeff=None, stream=None) -> dict:
+    """One-shot RT0 assembly -> dict(rowptr, colidx, K, M) of CUDA tensors."""
+    return _one_shot("rt0_assemble", dim, nodes, elems, coeff, stream)
+
+
+def ned_assemble(dim: int, nodes: torch.Tensor, elems: torch.Tensor, coeff=None, stream=None) -> dict:
+    """One-shot Nedelec assembly -> dict(rowptr, colidx, K, M) of CUDA tensors."""
+    return _one_shot("ned_assemble", dim, nodes, elems, coeff, stream)
+
+
+class Plan:
+    """A per-mesh plan (topology + CSR pattern) and the calls that use it."""
+
+    def __init__(self, kind: int, dim: int, n_nodes: int, elems: torch.Tensor, stream=None):
+        self.kind, self.dim, self.n_nodes = kind, dim, int(n_nodes)
+        self.n_elems = int(elems.shape[0])
+        self.device = elems.device
+        self._h = ef_plan_create(kind, dim, n_nodes, elems, stream)
+        self.n_dofs, self.nnz = ef_plan_sizes(self._h)
+        self.nloc = 3 if dim == 2 else (4 if kind == EF_RT0 else 6)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("plan is closed")
+        return self._h
+
+    def info(self) -> dict:
+        return ef_plan_info(self.handle)
+
+    def set_block(self, block: int, stream=None):
+        ef_plan_set_block(self.handle, block, stream)
+
+    def pattern(self, stream=None):
+        rowptr = torch.empty(self.n_dofs + 1, dtype=torch.int64, device=self.device)
+        colidx = torch.empty(max(self.nnz, 0), dtype=torch.int32, device=self.device)
+        ef_plan_pattern(self.handle, rowptr, colidx, stream)
+        return rowptr, colidx
+
+    def topology(self, stream=None):
+        e2d = torch.empty((self.n_elems, self.nloc), dtype=torch.int32, device=self.device)
+        sb = torch.empty(self.n_elems, dtype=torch.uint8, device=self.device)
+        ent = 3 if (self.kind == EF_RT0 and self.dim == 3) else 2
+        d2n = torch.empty((self.n_dofs, ent), dtype=torch.int32, device=self.device)
+        ef_plan_topology(self.handle, e2d, sb, d2n, stream)
+        return e2d, sb, d2n
+
+    def _vals(self, K, M):
+        if K is None:
+            K = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        if M is None:
+            M = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        return K, M
+
+    def assemble(self, nodes, coeff=None, K=None, M=None, stream=None):
+        K, M = self._vals(K, M)
+        ef_assemble(self.handle, nodes, coeff, K, M, stream)
+        return K, M
+
+    def assemble_two_pass(self, nodes, coeff=None, K=None, M=None, stream=None):
+        K, M = self._vals(K, M)
+        ef_assemble_two_pass(self.handle, nodes, coeff, K, M, stream)
+        return K, M
+
+    def assemble_host(self, nodes, coeff=None, K=None, M=None, stream=None):
+        if K is None:
+            K = torch.empty(self.nnz, dtype=torch.float64, pin_memory=True)
+        if M is None:
+            M = torch.empty(self.nnz, dtype=torch.float64, pin_memory=True)
+        ef_assemble_host(self.handle, nodes, coeff, K, M, stream)
+        return K, M
+
+    def adjoint(self, nodes, coeff, u, v, stream=None):
+        """(J, dJ/dnodes, dJ/dcoeff) of J = u^T K u + v^T M v (3D Nedelec)."""
+        J = torch.empty(1, dtype=torch.float64, device=self.device)
+        gx = torch.empty((self.n_nodes, self.dim), dtype=torch.float64, device=self.device)
+        gs = torch.empty(self.n_elems, dtype=torch.float64, device=self.device)
+        ef_adjoint(self.handle, nodes, coeff, u, v, J, gx, gs, stream)
+        return J, gx, gs
+
+    def check(self, stream=None):
+        ef_plan_check(self.handle, stream)
+
+    def close(self):
+        if self._h is not None:
+            ef_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

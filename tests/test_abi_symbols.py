@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every function declared in
+include/*.h (no GPU needed: nothing is computed here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char|double|int64_t)\s*\**\s*(\w+)\s*\(", text, re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ef_plan_create", "ef_assemble", "rt0_assemble", "ned_assemble", "ef_plan_pattern",
+                     "ef_plan_topology", "ef_plan_destroy", "ef_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1409_4618_gb300 import build
+
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    lib = ef.load()
+    assert lib.ef_status_string(ef.EF_ERR_DEGENERATE).decode().startswith("degenerate")
+    assert lib.ef_status_string(12345).decode() == "unknown status"
+
+
+def test_argument_errors_need_no_gpu():
+    """Argument checks run before any CUDA call."""
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    lib = ef.load()
+    h = ctypes.c_void_p()
+    assert lib.ef_plan_create(3, 3, 10, 1, None, None, ctypes.byref(h)) == ef.EF_ERR_ARG      # bad kind
+    assert lib.ef_plan_create(1, 4, 10, 1, None, None, ctypes.byref(h)) == ef.EF_ERR_ARG      # bad dim
+    assert lib.ef_plan_create(1, 3, 10, 5, None, None, ctypes.byref(h)) == ef.EF_ERR_ARG      # no elements
+    assert lib.ef_plan_create(1, 3, 2642246, 1, ctypes.c_void_p(16), None,
+                              ctypes.byref(h)) == ef.EF_ERR_KEY_OVERFLOW
+    assert lib.ef_plan_create(2, 3, 1 << 31, 1, ctypes.c_void_p(16), None, ctypes.byref(h)) == ef.EF_ERR_SIZE
+    assert lib.ef_plan_create(2, 3, 100, 1 << 28, ctypes.c_void_p(16), None, ctypes.byref(h)) == ef.EF_ERR_SIZE
+    assert lib.ef_assemble(None, None, None, None, None, None) == ef.EF_ERR_ARG
+    assert h.value is None

@@ -1,0 +1,215 @@
+"""GPU parity against the oracle, through the C ABI (needs a GB300).
+
+Topology (elem2dof, sign bits, dof2nodes) and the CSR pattern must be bit for
+bit the oracle's; K and M values within 1e-12 of the entry scale defined in
+tests/_parity.py. Sizes span many 256-element tiles with ragged tails; local
+node order and element order are shuffled so that det B_K takes both signs;
+edge cases: one element, no element, unused nodes, the L-shaped domain. Every
+assembly path (pipelined default, plain two-pass, element-block with 128 or
+256 elements per CTA) is checked, and the default path also inside a CUDA
+graph.
+"""
+import numpy as np
+import pytest
+
+from paper_1409_4618_gb300 import meshgen as mg
+from tests._parity import compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+RT0, NED1 = 1, 2
+
+
+def _case(name):
+    if name == "c1_rt2d_32":               # the 2D RT0 workload: 32x32 squares, unit coefficient, no jitter
+        nodes, elems = mg.kuhn_square(32)
+        return RT0, 2, nodes, elems, None
+    if name == "ned2d_33_shuffled":
+        nodes, elems = mg.kuhn_square(33, 0.2, 7)
+        elems = mg.shuffle_local_order(elems, 7)
+        return NED1, 2, nodes, elems, mg.log_uniform_coeff(7, elems.shape[0])
+    if name == "rt2d_37_shuffled":
+        nodes, elems = mg.kuhn_square(37, 0.2, 8)
+        elems = mg.shuffle_local_order(elems, 8)
+        return RT0, 2, nodes, elems, mg.log_uniform_coeff(8, elems.shape[0])
+    if name == "ned3d_8":
+        nodes, elems = mg.kuhn_cube(8, 0.2, 2)
+        return NED1, 3, nodes, elems, mg.log_uniform_coeff(2, elems.shape[0])
+    if name == "ned3d_13_shuffled":
+        nodes, elems = mg.kuhn_cube(13, 0.2, 9)
+        elems = mg.shuffle_local_order(elems, 9)
+        perm = np.argsort(mg.uniform(9, 11, np.arange(elems.shape[0])))
+        return NED1, 3, nodes, elems[perm], mg.log_uniform_coeff(9, elems.shape[0])
+    if name == "rt3d_8":
+        nodes, elems = mg.kuhn_cube(8, 0.2, 3)
+        return RT0, 3, nodes, elems, mg.log_uniform_coeff(3, elems.shape[0])
+    if name == "rt3d_13_shuffled":
+        nodes, elems = mg.kuhn_cube(13, 0.2, 10)
+        elems = mg.shuffle_local_order(elems, 10)
+        perm = np.argsort(mg.uniform(10, 11, np.arange(elems.shape[0])))
+        return RT0, 3, nodes, elems[perm], mg.log_uniform_coeff(10, elems.shape[0])
+    if name == "lshape_4_ned2d":
+        nodes, elems = mg.lshape(4)
+        return NED1, 2, nodes, elems, None
+    raise KeyError(name)
+
+
+CASES = ["c1_rt2d_32", "ned2d_33_shuffled", "rt2d_37_shuffled", "ned3d_8", "ned3d_13_shuffled", "rt3d_8",
+         "rt3d_13_shuffled", "lshape_4_ned2d"]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("path", ["default", "two_pass", "blocked128", "blocked256"])
+def test_parity(ora, name, path):
+    kind, dim, nodes, elems, coeff = _case(name)
+    o = ora.assemble(kind, dim, nodes, elems, coeff)
+    g = run_gpu(kind, dim, nodes, elems, coeff, path=path)
+    compare(g, o)
+
+
+@pytest.mark.parametrize("kind,dim", [(RT0, 2), (NED1, 2), (RT0, 3), (NED1, 3)])
+def test_single_element_and_unused_nodes(ora, kind, dim):
+    rng = np.random.default_rng(5)
+    nodes = rng.random((9, dim))
+    elems = np.array([[7, 2, 5] + ([1] if dim == 3 else [])], dtype=np.int32)
+    o = ora.assemble(kind, dim, nodes, elems, np.array([2.5]))
+    g = run_gpu(kind, dim, nodes, elems, np.array([2.5]))
+    compare(g, o)
+
+
+@pytest.mark.parametrize("kind,dim", [(RT0, 2), (NED1, 3)])
+def test_empty_mesh(kind, dim):
+    nodes = np.zeros((4, dim))
+    elems = np.zeros((0, dim + 1), dtype=np.int32)
+    g = run_gpu(kind, dim, nodes, elems)
+    assert g["n_dofs"] == 0 and g["nnz"] == 0
+    np.testing.assert_array_equal(g["rowptr"], [0])
+
+
+@pytest.mark.parametrize("kind", [NED1, RT0])
+def test_paths_agree_bitwise_and_runs_repeat(ora, kind):
+    """Pipelined (several element chunks at 131,712 tets), plain two-pass and
+    element-block paths form the same sums in the same order: identical bits,
+    run after run; and the pipelined result passes parity."""
+    nodes, elems = mg.kuhn_cube(28, 0.2, 12)
+    coeff = mg.log_uniform_coeff(12, elems.shape[0])
+    a = run_gpu(kind, 3, nodes, elems, coeff, path="default")
+    b = run_gpu(kind, 3, nodes, elems, coeff, path="two_pass")
+    c = run_gpu(kind, 3, nodes, elems, coeff, path="default")
+    d = run_gpu(kind, 3, nodes, elems, coeff, path="blocked128")
+    for key in ("K", "M"):
+        for other in (b, c, d):
+            assert np.array_equal(a[key].view(np.uint64), other[key].view(np.uint64))
+    compare(a, ora.assemble(kind, 3, nodes, elems, coeff))
+
+
+def test_csr_is_symmetric_bitwise():
+    kind, dim, nodes, elems, coeff = _case("rt3d_13_shuffled")
+    g = run_gpu(kind, dim, nodes, elems, coeff)
+    rows = np.repeat(np.arange(g["n_dofs"]), np.diff(g["rowptr"]))
+    cols = g["colidx"]
+    order = np.lexsort((rows, cols))          # transposed order
+    for key in ("K", "M"):
+        v = g[key]
+        # entry (i,j) equals entry (j,i) bit for bit
+        idx = np.lexsort((cols, rows))
+        assert np.array_equal(idx, np.arange(len(v)))
+        t = v[order]
+        assert np.array_equal(v.view(np.uint64), t.view(np.uint64))
+
+
+def test_one_shot_and_host_path_match_plan(ora):
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    kind, dim, nodes, elems, coeff = _case("ned3d_8")
+    g = run_gpu(kind, dim, nodes, elems, coeff)
+    tn, te, tc = (torch.from_numpy(x).cuda() for x in (nodes, elems, coeff))
+    one = ef.ned_assemble(3, tn, te, tc)
+    np.testing.assert_array_equal(one["rowptr"].cpu().numpy(), g["rowptr"])
+    np.testing.assert_array_equal(one["colidx"].cpu().numpy(), g["colidx"])
+    np.testing.assert_array_equal(one["K"].cpu().numpy(), g["K"])
+    np.testing.assert_array_equal(one["M"].cpu().numpy(), g["M"])
+    plan = ef.Plan(kind, dim, nodes.shape[0], te)
+    hn = torch.from_numpy(nodes).pin_memory()
+    hc = torch.from_numpy(coeff).pin_memory()
+    K, M = plan.assemble_host(hn, hc)
+    np.testing.assert_array_equal(K.numpy(), g["K"])
+    np.testing.assert_array_equal(M.numpy(), g["M"])
+    plan.close()
+    rt = ef.rt0_assemble(2, *(torch.from_numpy(x).cuda() for x in mg.kuhn_square(5)))
+    o = ora.assemble(RT0, 2, *mg.kuhn_square(5))
+    np.testing.assert_array_equal(rt["colidx"].cpu().numpy(), o["colidx"])
+    assert np.abs(rt["K"].cpu().numpy() - o["K"]).max() <= 1e-12 * np.abs(o["K"]).max()
+
+
+def test_errors_are_reported():
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(2)
+    te = torch.from_numpy(elems).cuda()
+    bad = elems.copy()
+    bad[5, 1] = nodes.shape[0]                       # node id out of range
+    with pytest.raises(ef.EdgeFemError) as e:
+        ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(bad).cuda())
+    assert e.value.code == ef.EF_ERR_RANGE
+    bad = elems.copy()
+    bad[3, 2] = bad[3, 0]                            # repeated node
+    with pytest.raises(ef.EdgeFemError) as e:
+        ef.Plan(RT0, 3, nodes.shape[0], torch.from_numpy(bad).cuda())
+    assert e.value.code == ef.EF_ERR_ARG
+    flat = nodes.copy()
+    flat[:, 2] = 0.5                                 # every element degenerate
+    plan = ef.Plan(NED1, 3, nodes.shape[0], te)
+    plan.assemble(torch.from_numpy(flat).cuda())
+    with pytest.raises(ef.EdgeFemError) as e:
+        plan.check()
+    assert e.value.code == ef.EF_ERR_DEGENERATE
+    plan.check()                                     # the status word was cleared
+    plan.assemble(torch.from_numpy(nodes).cuda())
+    plan.check()
+    plan.close()
+    with pytest.raises(ef.EdgeFemError) as e:
+        ef.rt0_assemble(3, torch.from_numpy(flat).cuda(), te)
+    assert e.value.code == ef.EF_ERR_DEGENERATE
+
+
+def test_cuda_graph_capture_replays_bitwise():
+    """ef_assemble (the pipelined fork/join across two streams) captured in a
+    CUDA graph and replayed gives the same bits as a direct call."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(28, 0.2, 13)
+    coeff = mg.log_uniform_coeff(13, elems.shape[0])
+    tn, tc = torch.from_numpy(nodes).cuda(), torch.from_numpy(coeff).cuda()
+    plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).cuda())
+    assert plan.info()["pipeline_chunks"] > 1
+    K0, M0 = plan.assemble(tn, tc)
+    K = torch.zeros_like(K0)
+    M = torch.zeros_like(M0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        plan.assemble(tn, tc, K, M, stream=s)            # warm-up outside the capture
+        s.synchronize()
+        K.zero_()
+        M.zero_()
+        with torch.cuda.graph(g, stream=s):
+            plan.assemble(tn, tc, K, M, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(K.view(torch.int64), K0.view(torch.int64))
+    assert torch.equal(M.view(torch.int64), M0.view(torch.int64))
+    tn.mul_(1.5)                                          # new coordinates in place, replay again
+    g.replay()
+    K1, M1 = plan.assemble(tn, tc)
+    torch.cuda.synchronize()
+    assert torch.equal(K.view(torch.int64), K1.view(torch.int64))
+    plan.check()
+    plan.close()
