@@ -158,6 +158,37 @@ int ef_assemble_two_pass(const ef_plan* plan, const double* d_nodes, const doubl
 int ef_assemble_host(ef_plan* plan, const double* h_nodes, const double* h_coeff, double* h_Kval, double* h_Mval,
                      void* stream);
 
+/*
+ * ef_assemble_noalloc -- the paper has no counterpart to this call; it is
+ * for callers that must not allocate device memory while they assemble:
+ * code running while a CUDA stream capture is open in global mode (any
+ * cudaMalloc in the process would break that capture), loops with a latency
+ * budget that cannot absorb the device-wide synchronisation a cudaMalloc or
+ * cudaFree may cause, and applications whose device memory belongs to
+ * another allocator with a fixed budget.
+ *
+ * Same result as ef_assemble (the same sums in the same order, so the same
+ * bits), computed by the two-pass kernels with the element matrices kept in
+ * one library-wide static device array of EF_NOALLOC_SCRATCH_BYTES instead
+ * of the plan's own scratch. No cudaMalloc, cudaFree or other allocating
+ * routine is called. The array exists on every GPU that loads the library
+ * and stays there until the process exits.
+ *   Limit: n_elems * nloc (nloc+1)/2 * 16 bytes must fit in the array
+ *   (3D Nedelec: 199,728 elements; 3D RT0: 419,430; 2D: 699,050); larger
+ *   plans get EF_ERR_SIZE and nothing is launched.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ *   Every call uses the same array and leaves its contents there; nothing in
+ *   it has to start at zero, because each call overwrites every entry it
+ *   reads. Calls whose work overlaps on the GPU (on different streams, or on
+ *   plans of different threads) race on the array.
+ * Asynchronous on `stream`. Other errors: EF_ERR_ARG, EF_ERR_CUDA.
+ */
+#define EF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int ef_assemble_noalloc(const ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval,
+                        double* d_Mval, void* stream);
+
 /* Synchronise `stream`, then read and clear the plan's device status word:
  * EF_ERR_DEGENERATE if an element with det B_K = 0 was met since the last
  * check, EF_ERR_TIMEOUT if a bounded wait gave up, else EF_OK. */

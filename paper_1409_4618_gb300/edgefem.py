@@ -84,6 +84,7 @@ def load():
             "ef_assemble": ([P, P, P, P, P, P], I),
             "ef_assemble_two_pass": ([P, P, P, P, P, P], I),
             "ef_assemble_host": ([P, P, P, P, P, P], I),
+            "ef_assemble_noalloc": ([P, P, P, P, P, P], I),
             "ef_plan_check": ([P, P], I),
             "ef_adjoint": ([P, P, P, P, P, P, P, P, P], I),
             "ef_plan_destroy": ([P], None),
@@ -170,6 +171,11 @@ def ef_assemble(plan, nodes, coeff, K, M, stream=None):
 def ef_assemble_two_pass(plan, nodes, coeff, K, M, stream=None):
     _check(load().ef_assemble_two_pass(plan, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
                                        _dev(K, torch.float64, "K"), _dev(M, torch.float64, "M"), _stream_ptr(stream)))
+
+
+def ef_assemble_noalloc(plan, nodes, coeff, K, M, stream=None):
+    _check(load().ef_assemble_noalloc(plan, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
+                                      _dev(K, torch.float64, "K"), _dev(M, torch.float64, "M"), _stream_ptr(stream)))
 
 
 def ef_assemble_host(plan, nodes, coeff, K, M, stream=None):
