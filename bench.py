@@ -114,14 +114,15 @@ class ClockSampler:
 
 
 def fp64_ops_per_element(kind: int, dim: int) -> int:
-    """FP64 pipe operations (DADD/DMUL/DFMA each 1) of one element's local
+    """FP64 pipe operations (DADD, DMUL, DFMA each 1) of one element's local
     matrices in the closed forms of csrc/ef_element.cuh, counted from the
-    source; the reciprocal / rsqrt is counted as 10."""
+    source; the library reciprocal 1/|det| is counted as 8."""
     if (kind, dim) == (2, 3):
-        # B 9, H 18, adj(H) 12, det H 3, rsqrt 10, scales 2, K: 6 + 15, M: 7 + 6 + 8 + 6*3 + 15*3
-        return 9 + 18 + 12 + 3 + 10 + 2 + 21 + 7 + 6 + 8 + 18 + 45
+        # B 9, H 18, adj(H) 12, det 9, 1/|det| 8, sigma*r 1, K: 1 + 6 + 15, M: 1 + 6 + 8 + 48
+        return 9 + 18 + 12 + 9 + 8 + 1 + 22 + 63
     if (kind, dim) == (1, 3):
-        return 9 + 18 + 9 + 10 + 1 + 6 + 5 + 4 + 3 + 3 + 3 + 15 + 1
+        # B 9, H 18, det 9, 1/|det| 8, sigma*r 1, row sums 6, c0 5, scales 5, q 3, t 3, entries 12, K 1
+        return 9 + 18 + 9 + 8 + 1 + 6 + 5 + 5 + 3 + 3 + 12 + 1
     return 40
 
 
@@ -154,6 +155,97 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_batched(args, dev, plain_rate):
+    """256 independent cubes, n ~ U{8..48} (seed 4, mesh b jittered with seed
+    4000 + b), all assembled by one persistent launch per step; schedule picked
+    by the library's autotuner. Rate = all elements of the batch per second."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    sizes = mg.batch_sizes(4, args.batch_meshes, 8, 48)
+    nodes, elems, coeff = [], [], []
+    for b, n in enumerate(sizes):
+        nd, el = mg.kuhn_cube(int(n), 0.2, 4000 + b)
+        nodes.append(torch.from_numpy(nd).to(dev))
+        elems.append(torch.from_numpy(el).to(dev))
+        coeff.append(torch.from_numpy(mg.log_uniform_coeff(4000 + b, el.shape[0])).to(dev))
+    t0 = time.perf_counter()
+    batch = ef.Batch(2, 3, [x.shape[0] for x in nodes], elems)
+    plan_s = time.perf_counter() - t0
+    K = [torch.empty(z, dtype=torch.float64, device=dev) for z in batch.nnz]
+    M = [torch.empty(z, dtype=torch.float64, device=dev) for z in batch.nnz]
+    batch.bind(nodes, coeff, K, M)
+    t0 = time.perf_counter()
+    cfg = batch.tune(reps=2)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        batch.assemble(stream)
+    batch.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.batch_steps):
+        batch.assemble(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch.check()
+    ms = e0.elapsed_time(e1) / args.batch_steps
+    T = int(sum(batch.n_elems))
+    rate = T / (ms / 1e3) / 1e6
+    out = {"value": rate, "unit": UNIT, "meshes": len(sizes), "elements": T, "nnz": int(sum(batch.nnz)),
+           "ms_per_launch": ms, "launches_per_step": 1, "vs_plain": rate / plain_rate,
+           "plain": "the single-mesh ef_assemble rate of this run", "config": cfg,
+           "plan_s": plan_s, "tune_s": tune_s}
+    batch.close()
+    return out
+
+
+def run_adjoint(args, dev):
+    """Adjoint of u^T K u + v^T M v on the 96^3 Nedelec workload (5,308,416
+    tets, seed 5), against plain ef_assemble on the same mesh."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(96, 0.2, 5)
+    coeff = mg.log_uniform_coeff(5, elems.shape[0])
+    tn, tc = torch.from_numpy(nodes).to(dev), torch.from_numpy(coeff).to(dev)
+    plan = ef.Plan(2, 3, nodes.shape[0], torch.from_numpy(elems).to(dev))
+    u = torch.from_numpy(mg.normal(5, mg.STREAM_U, plan.n_dofs)).to(dev)
+    v = torch.from_numpy(mg.normal(5, mg.STREAM_V, plan.n_dofs)).to(dev)
+    J = torch.empty(1, dtype=torch.float64, device=dev)
+    gx = torch.empty_like(tn)
+    gs = torch.empty_like(tc)
+    K = torch.empty(plan.nnz, dtype=torch.float64, device=dev)
+    M = torch.empty_like(K)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    ms_adj = timed(lambda: ef.ef_adjoint(plan.handle, tn, tc, u, v, J, gx, gs, stream), args.adjoint_steps)
+    ms_asm = timed(lambda: ef.ef_assemble(plan.handle, tn, tc, K, M, stream), args.adjoint_steps)
+    plan.check()
+    T = elems.shape[0]
+    out = {"value": T / (ms_adj / 1e3) / 1e6, "unit": UNIT, "workload": "ned3d_kuhn96_jitter0.2",
+           "elements": int(T), "ms_per_step": ms_adj,
+           "plain_same_mesh": {"value": T / (ms_asm / 1e3) / 1e6, "ms_per_step": ms_asm},
+           "vs_plain": ms_asm / ms_adj}
+    plan.close()
+    return out
 
 
 def cpu_baseline():
@@ -195,8 +287,11 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     path = args.path
+    tuned = None
     if path.startswith("blocked"):
         plan.set_block(int(path[len("blocked"):]))
+    elif path == "default":
+        tuned = plan.tune(tn, tc, K, M, reps=5)      # library autotuner: pipeline chunks / element-block
 
     def step():
         if path == "two_pass":
@@ -275,15 +370,19 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "elements": T, "nodes": V, "dofs": plan.n_dofs, "nnz": nnz,
-                   "path": path, "plan": info, "parallelism": "replicas" if ws > 1 else "single",
+                   "path": path, "tuned_choice": tuned, "plan": info, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": f"no flush: each step moves {alg_bytes / 1e6:.0f} MB (algorithmic) > 129 MB L2"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
     }
+    plan.close()
+    if not args.no_batched:
+        line["batched"] = run_batched(args, dev, value / ws)
+    if not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -297,6 +396,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--path", default="default", choices=["default", "two_pass", "blocked128", "blocked256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--batch-meshes", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--adjoint-steps", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

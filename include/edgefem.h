@@ -98,7 +98,7 @@ typedef struct {
     int32_t fused_block;          /* elements per CTA of the element-block path if selected, else 0 */
     int64_t fused_blocks;
     int64_t fused_partial;        /* element-block path: contributions summed by the fix-up */
-    int32_t pipeline_chunks;      /* element chunks of the pipelined path (1: not pipelined) */
+    int32_t pipeline_chunks;      /* element chunks of the pipelined path (1: plain two-pass order) */
 } ef_plan_info_t;
 int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info);
 
@@ -110,6 +110,19 @@ int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info);
  * speed differs. Synchronises `stream` and allocates when building the
  * block schedule. Errors: EF_ERR_ARG, EF_ERR_OOM. */
 int ef_plan_set_block(ef_plan* plan, int block, void* stream);
+
+/* Select the pipelined path with `chunks` element chunks (1 = the plain
+ * two-pass order on one stream, up to 16). Results do not depend on it.
+ * Synchronises `stream`; reallocates the plan's work-order arrays. */
+int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream);
+
+/* Autotuner for ef_assemble on this plan: times `reps` calls of each
+ * candidate (pipelines of 1, 2, 3, 4, 6, 8 chunks of at least 64K elements;
+ * element-block path with 128 or 256 elements per CTA) on the given buffers,
+ * keeps the fastest and reports it in *chosen (chunks, or -block) if not
+ * NULL. Overwrites d_Kval / d_Mval. Synchronises `stream`. */
+int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
+                 int reps, int* chosen, void* stream);
 
 /* Copy the CSR pattern into caller buffers: d_rowptr [n_dofs+1] int64,
  * d_colidx [nnz] int32 (device). Asynchronous on `stream`. */
@@ -127,8 +140,9 @@ int ef_plan_topology(const ef_plan* plan, int32_t* d_elem2dof, uint8_t* d_signbi
  * Assemble K and M values into caller-owned CSR value arrays (pattern of
  * ef_plan_pattern): local matrices by the closed forms of the Sec. 2.4
  * integrals on every element, then the fixed-order sum into each nonzero.
- * The element kernel runs in chunks on `stream`; the sums of the nonzeros a
- * chunk completes run on a plan-owned stream while the next chunk computes
+ * With more than one pipeline chunk (ef_plan_set_pipeline, ef_plan_tune),
+ * the element kernel runs in chunks on `stream` and the sums of the nonzeros
+ * a chunk completes run on a plan-owned stream while the next chunk computes
  * (joined back into `stream` by events, so the call is one unit of work on
  * `stream` and captures into a CUDA graph as a fork/join).
  *   d_nodes: n_nodes x dim doubles; d_coeff: n_elems doubles or NULL (= 1);
@@ -210,6 +224,57 @@ void ef_plan_destroy(ef_plan* plan);
  */
 int ef_adjoint(const ef_plan* plan, const double* d_nodes, const double* d_coeff, const double* d_u,
                const double* d_v, double* d_J, double* d_grad_nodes, double* d_grad_coeff, void* stream);
+
+/* ---- batched assembly of many meshes ---------------------------------------- */
+
+/*
+ * A batch holds independent meshes of one kind and dimension, each with its
+ * own plan and its own CSR. ef_batch_assemble assembles all of them in ONE
+ * persistent kernel launch: a queue hands out every (mesh, element tile)
+ * before any (mesh, sum tile); a sum tile starts once its mesh's element
+ * tiles are done (a bounded wait; EF_ERR_TIMEOUT from ef_batch_check if a
+ * wait gave up). Values are those of ef_assemble on each mesh, bit for bit.
+ */
+typedef struct ef_batch ef_batch;
+
+/* Schedule of the persistent launch (chosen by ef_batch_tune). */
+typedef struct {
+    int32_t elems_per_tile;  /* elements per element tile = threads per CTA: 128 or 256 */
+    int32_t sum_tile;        /* upper nonzeros per sum tile */
+    int32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x number of SMs */
+    int32_t dynamic;         /* 1: tiles by an integer ticket; 0: static stride blockIdx + k gridDim */
+    int32_t largest_first;   /* 1: meshes in order of decreasing size; 0: as given */
+} ef_batch_config_t;
+
+/* Build the per-mesh plans (as ef_plan_create for each). n_nodes, n_elems:
+ * host arrays [n_meshes]; d_elems: host array of n_meshes device pointers.
+ * Synchronises `stream`. Errors as ef_plan_create. */
+int ef_batch_create(int kind, int dim, int n_meshes, const int64_t* n_nodes, const int64_t* n_elems,
+                    const int32_t* const* d_elems, void* stream, ef_batch** out);
+/* Per-mesh sizes into host arrays [n_meshes] (either may be NULL). */
+int ef_batch_sizes(const ef_batch* batch, int64_t* n_dofs, int64_t* nnz);
+/* CSR pattern of one mesh (as ef_plan_pattern). */
+int ef_batch_pattern(const ef_batch* batch, int mesh, int64_t* d_rowptr, int32_t* d_colidx, void* stream);
+/* Bind the per-mesh device buffers used by ef_batch_assemble: host arrays
+ * [n_meshes] of device pointers to nodes (n_nodes x dim), coefficients
+ * (n_elems, or a NULL array / NULL entries for 1) and K, M values (nnz).
+ * Copies the pointer tables to the device and synchronises `stream`. */
+int ef_batch_bind(ef_batch* batch, const double* const* d_nodes, const double* const* d_coeff, double* const* d_K,
+                  double* const* d_M, void* stream);
+/* One persistent launch assembling every mesh into its bound buffers.
+ * Asynchronous, no allocation, no host synchronisation; capturable in a CUDA
+ * graph. Calls that overlap on the GPU race. EF_ERR_ARG if nothing is bound. */
+int ef_batch_assemble(const ef_batch* batch, void* stream);
+/* Autotuner: times each candidate schedule `reps` times on the bound buffers
+ * (elements per tile 128/256, sum tiles 512/2048/8192 nonzeros, full or half
+ * occupancy, dynamic or static, given or largest-first mesh order) and keeps
+ * the fastest; writes it to *best (may be NULL). Overwrites the bound K, M. */
+int ef_batch_tune(ef_batch* batch, int reps, ef_batch_config_t* best, void* stream);
+int ef_batch_get_config(const ef_batch* batch, ef_batch_config_t* cfg);
+int ef_batch_set_config(ef_batch* batch, const ef_batch_config_t* cfg, void* stream);
+/* Synchronise `stream`; EF_ERR_DEGENERATE / EF_ERR_TIMEOUT if met since the last check. */
+int ef_batch_check(ef_batch* batch, void* stream);
+void ef_batch_destroy(ef_batch* batch);
 
 /* ---- one-shot convenience calls ------------------------------------------ */
 

@@ -16,7 +16,7 @@ void free_plan_memory(ef_plan* p)
                     p->d_local,     p->d_status,     p->d_fb_slot_off, p->d_fb_sinfo, p->d_fb_cidx,
                     p->d_fb_posA,   p->d_fb_posB,    p->d_px_uid,
                     p->d_stage_nodes, p->d_stage_coeff, p->d_stage_K, p->d_stage_M,
-                    p->d_node_off,  p->d_node_inc,   p->d_adj_part,  p->d_adj_jpart, p->d_uorder};
+                    p->d_node_off,  p->d_node_inc,   p->d_adj_part,  p->d_adj_jpart};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -33,10 +33,12 @@ int plan_args(int kind, int dim, int64_t n_nodes, int64_t n_elems, const void* d
     return EF_OK;
 }
 
-int create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, cudaStream_t s, ef_plan** out)
+int create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, cudaStream_t s, int flags,
+           ef_plan** out)
 {
     ef_plan* p = (ef_plan*)calloc(1, sizeof(ef_plan));
     if (!p) return EF_ERR_OOM;
+    p->flags = flags;
     p->kind = kind;
     p->dim = dim;
     p->variant = variant_of(kind, dim);
@@ -72,12 +74,12 @@ int create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d
             st = EF_ERR_OOM;
             break;
         }
-        if ((st = build_scatter_order(p, s)) != EF_OK) break;
-        if ((st = build_adjoint(p, s)) != EF_OK) break;
+        if ((st = build_work_order(p, default_pipeline_chunks(p), s)) != EF_OK) break;
+        if (!(flags & EF_PLAN_NO_ADJOINT) && (st = build_adjoint(p, s)) != EF_OK) break;
     } while (0);
     if (st != EF_OK) {
         cudaStreamSynchronize(s);
-        destroy_pipeline(p);
+        release_work_order(p);
         free_plan_memory(p);
         free(p);
         return st;
@@ -128,6 +130,18 @@ int one_shot(int kind, int dim, const double* d_nodes, int64_t n_nodes, const in
 
 }  // namespace
 
+namespace ef {
+int plan_create_internal(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, cudaStream_t s,
+                         int flags, ef_plan** out)
+{
+    if (!out) return EF_ERR_ARG;
+    *out = nullptr;
+    int st = plan_args(kind, dim, n_nodes, n_elems, d_elems);
+    if (st != EF_OK) return st;
+    return create(kind, dim, n_nodes, n_elems, d_elems, s, flags, out);
+}
+}  // namespace ef
+
 extern "C" {
 
 int ef_plan_create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, void* stream,
@@ -137,7 +151,7 @@ int ef_plan_create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const in
     *out = nullptr;
     int st = plan_args(kind, dim, n_nodes, n_elems, d_elems);
     if (st != EF_OK) return st;
-    return create(kind, dim, n_nodes, n_elems, d_elems, (cudaStream_t)stream, out);
+    return create(kind, dim, n_nodes, n_elems, d_elems, (cudaStream_t)stream, 0, out);
 }
 
 int ef_plan_sizes(const ef_plan* plan, int64_t* n_dofs, int64_t* nnz)
@@ -180,6 +194,59 @@ int ef_plan_set_block(ef_plan* plan, int block, void* stream)
     EF_TRY(build_fused_block(plan, block, (cudaStream_t)stream));
     plan->use_blocked = 1;
     return EF_OK;
+}
+
+int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream)
+{
+    if (!plan || chunks < 1 || chunks > EF_MAX_CHUNKS) return EF_ERR_ARG;
+    if (plan->flags & EF_PLAN_NO_PIPELINE) return EF_ERR_ARG;
+    EF_TRY(build_work_order(plan, chunks, (cudaStream_t)stream));
+    plan->use_blocked = 0;
+    return EF_OK;
+}
+
+int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
+                 int reps, int* chosen, void* stream)
+{
+    EF_TRY(assemble_checks(plan, d_nodes, d_Kval, d_Mval));
+    if (plan->flags & EF_PLAN_NO_PIPELINE) return EF_ERR_ARG;
+    if (reps < 1) reps = 5;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    EF_CUDA(cudaEventCreate(&e0));
+    EF_CUDA(cudaEventCreate(&e1));
+    // candidates: pipelines of 1..8 chunks (chunks of at least 64K elements), element-block 128 / 256
+    const int cand[] = {1, 2, 3, 4, 6, 8, -128, -256};
+    int best = 1, st = EF_OK;
+    float best_ms = 1e30f;
+    for (int c : cand) {
+        if (c > 1 && plan->T / c < 65536) continue;
+        if (c > 0)
+            st = ef_plan_set_pipeline(plan, c, stream);
+        else
+            st = ef_plan_set_block(plan, -c, stream);
+        if (st != EF_OK) break;
+        if ((st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream)) != EF_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == EF_OK; r++) st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = EF_ERR_CUDA;
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != EF_OK) return st;
+    st = best > 0 ? ef_plan_set_pipeline(plan, best, stream) : ef_plan_set_block(plan, -best, stream);
+    if (st == EF_OK && chosen) *chosen = best;
+    return st == EF_OK ? ef_plan_check(plan, stream) : st;
 }
 
 int ef_plan_pattern(const ef_plan* plan, int64_t* d_rowptr, int32_t* d_colidx, void* stream)
@@ -276,7 +343,7 @@ void ef_plan_destroy(ef_plan* plan)
 {
     if (!plan) return;
     cudaDeviceSynchronize();
-    destroy_pipeline(plan);
+    release_work_order(plan);
     free_plan_memory(plan);
     free(plan);
 }

@@ -15,11 +15,17 @@
 // warp instruction holds the FP64 pipe for its full duration even when lanes
 // are idle) while memory accesses stay local.
 //
-// Pipelined form (ef_assemble): the element kernel runs chunk by chunk on the
-// caller's stream; after each chunk an event lets the plan's second stream
-// sum the nonzeros that chunk completed, while the next chunk computes. The
-// chunk's local matrices are still in L2 when they are read. The caller's
-// stream waits for the last sum before the call's work counts as done.
+// Layout: the contribution list is in the sum's work order (each item's
+// contributions contiguous, ascending element order inside, items one after
+// the other), and the element kernel writes each contribution straight to its
+// slot through the plan's inverse map; a warp of the sum then reads one
+// contiguous run and its per-item data (list start, CSR positions) coalesced.
+//
+// Pipelined form (ef_assemble with more than one chunk, ef_plan_set_pipeline):
+// the element kernel runs chunk by chunk on the caller's stream; after each
+// chunk an event lets the plan's sum stream add up the nonzeros that chunk
+// completed, while the next chunk computes; the caller's stream waits for the
+// last sum (fork/join by events).
 #include "ef_assemble.cuh"
 #include "ef_internal.cuh"
 
@@ -28,11 +34,15 @@ namespace {
 
 constexpr int TPB = 256;
 
+// Writes each contribution to its slot in the nonzero-ordered contribution
+// list: inv[q * T + e] = position of (element e, pair q). K values occupy
+// list[0, np T), M values list[np T, 2 np T).
 template <int VAR>
-__global__ void __launch_bounds__(TPB) k_element_local(const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(TPB, 4) k_element_local(const int32_t* __restrict__ elems,
                                                        const double* __restrict__ nodes,
-                                                       const double* __restrict__ coeff, int64_t e0, int64_t e1,
-                                                       int64_t T, double* __restrict__ local, int* status)
+                                                       const double* __restrict__ coeff,
+                                                       const uint32_t* __restrict__ inv, int64_t e0, int64_t e1,
+                                                       int64_t T, double* __restrict__ list, int* status)
 {
     using E = ElemTraits<VAR>;
     const int64_t e = e0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -40,10 +50,12 @@ __global__ void __launch_bounds__(TPB) k_element_local(const int32_t* __restrict
     double Kq[E::NP], Mq[E::NP];
     const double sigma = coeff ? __ldg(coeff + e) : 1.0;
     if (compute_element<VAR>(elems, nodes, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
+    const int64_t nK = (int64_t)E::NP * T;
 #pragma unroll
     for (int q = 0; q < E::NP; q++) {
-        local[(int64_t)q * T + e] = Kq[q];
-        local[(int64_t)(E::NP + q) * T + e] = Mq[q];
+        const uint32_t pos = __ldg(inv + (int64_t)q * T + e);
+        list[pos] = Kq[q];
+        list[nK + pos] = Mq[q];
     }
 }
 
@@ -60,31 +72,51 @@ __global__ void k_work_keys(const uint32_t* seg, const uint32_t* perm, int64_t U
     atomicAdd(&chunk_count[rc], 1u);
 }
 
-__global__ void __launch_bounds__(TPB) k_scatter(const uint32_t* __restrict__ order, int64_t w0, int64_t w1,
-                                                 const uint32_t* __restrict__ seg, const uint32_t* __restrict__ perm,
-                                                 const uint32_t* __restrict__ pos_up,
-                                                 const uint32_t* __restrict__ pos_lo,
-                                                 const double* __restrict__ localK, const double* __restrict__ localM,
+__global__ void k_work_items(const uint32_t* order, int64_t U, const uint32_t* seg, const uint32_t* pos_up,
+                             const uint32_t* pos_lo, uint32_t* wcnt, uint32_t* wpos_up, uint32_t* wpos_lo)
+{
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= U) return;
+    const uint32_t u = order[i];
+    wcnt[i] = seg[u + 1] - seg[u];
+    wpos_up[i] = pos_up[u];
+    wpos_lo[i] = pos_lo[u];
+}
+
+// inv[pair * T + element] = position of that contribution in the work-ordered list
+__global__ void k_work_inv(const uint32_t* order, int64_t U, const uint32_t* seg, const uint32_t* perm,
+                           const uint32_t* wseg, uint32_t* inv)
+{
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= U) return;
+    const uint32_t u = order[i];
+    const uint32_t s0 = seg[u], s1 = seg[u + 1], w0 = wseg[i];
+    for (uint32_t s = s0; s < s1; s++) inv[perm[s]] = w0 + (s - s0);
+}
+
+// Work item i sums list[wseg[i] .. wseg[i+1]): the contributions of one upper
+// nonzero, contiguous and in ascending element order; consecutive items are
+// consecutive in the list, so a warp reads one contiguous run.
+__global__ void __launch_bounds__(TPB) k_scatter(int64_t w0, int64_t w1, const uint32_t* __restrict__ wseg,
+                                                 const uint32_t* __restrict__ wpos_up,
+                                                 const uint32_t* __restrict__ wpos_lo,
+                                                 const double* __restrict__ listK, const double* __restrict__ listM,
                                                  double* __restrict__ K, double* __restrict__ M)
 {
     const int64_t i = w0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (i >= w1) return;
-    const uint32_t u = order[i];
-    const uint32_t s0 = seg[u], s1 = seg[u + 1];
-    uint32_t idx = perm[s0];
-    double k = localK[idx], m = localM[idx];
+    const uint32_t s0 = wseg[i], s1 = wseg[i + 1];
+    const uint32_t pu = wpos_up[i], pl = wpos_lo[i];
+    double k = listK[s0], m = listM[s0];
     for (uint32_t s = s0 + 1; s < s1; s++) {
-        idx = perm[s];
-        k += localK[idx];
-        m += localM[idx];
+        k += listK[s];
+        m += listM[s];
     }
-    uint32_t p = pos_up[u];
-    K[p] = k;
-    M[p] = m;
-    p = pos_lo[u];
-    if (p != 0xffffffffu) {
-        K[p] = k;
-        M[p] = m;
+    K[pu] = k;
+    M[pu] = m;
+    if (pl != 0xffffffffu) {
+        K[pl] = k;
+        M[pl] = m;
     }
 }
 
@@ -104,10 +136,10 @@ int element_range(const ef_plan* p, const double* nodes, const double* coeff, in
     if (e1 <= e0) return EF_OK;
     const unsigned grid = (unsigned)((e1 - e0 + TPB - 1) / TPB);
     switch (p->variant) {
-        case RT2: k_element_local<RT2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
-        case NED2: k_element_local<NED2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
-        case RT3: k_element_local<RT3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
-        default: k_element_local<NED3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT2: k_element_local<RT2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case NED2: k_element_local<NED2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT3: k_element_local<RT3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        default: k_element_local<NED3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
     }
     EF_CUDA(cudaGetLastError());
     return EF_OK;
@@ -119,9 +151,17 @@ int scatter_range(const ef_plan* p, int64_t w0, int64_t w1, double* K, double* M
     const unsigned grid = (unsigned)((w1 - w0 + TPB - 1) / TPB);
     const double* lK = p->d_local;
     const double* lM = p->d_local + (int64_t)p->np * p->T;
-    k_scatter<<<grid, TPB, 0, s>>>(p->d_uorder, w0, w1, p->d_seg, p->d_perm, p->d_pos_up, p->d_pos_lo, lK, lM, K, M);
+    k_scatter<<<grid, TPB, 0, s>>>(w0, w1, p->d_wseg, p->d_wpos_up, p->d_wpos_lo, lK, lM, K, M);
     EF_CUDA(cudaGetLastError());
     return EF_OK;
+}
+
+void free_work_order(ef_plan* p)
+{
+    void* ptrs[] = {p->d_wseg, p->d_wpos_up, p->d_wpos_lo, p->d_inv};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    p->d_wseg = p->d_wpos_up = p->d_wpos_lo = p->d_inv = nullptr;
 }
 
 }  // namespace
@@ -139,40 +179,75 @@ int order_by_count(const uint32_t* seg, uint32_t* list, int64_t n, uint64_t* key
     return EF_OK;
 }
 
-int build_scatter_order(ef_plan* p, cudaStream_t s)
+void destroy_pipeline(ef_plan* p)
 {
+    for (int c = 0; c < EF_MAX_CHUNKS + 2; c++)
+        if (p->pc_ev[c]) {
+            cudaEventDestroy(p->pc_ev[c]);
+            p->pc_ev[c] = nullptr;
+        }
+    if (p->pc_aux) cudaStreamDestroy(p->pc_aux);
+    p->pc_aux = nullptr;
     p->pc_chunks = 0;
+}
+
+// Work order and contribution-list layout for `nchunks` element chunks
+// (1 = plain two-pass): the order of the sums, their list ranges, CSR
+// positions, the element kernel's write positions, and the plan streams.
+int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
+{
+    destroy_pipeline(p);
+    free_work_order(p);
     if (p->U == 0) return EF_OK;
-    const int64_t U = p->U, T = p->T;
-    // chunks of at least 64K elements, at most EF_MAX_CHUNKS of them
-    int64_t chunk = (T + EF_MAX_CHUNKS - 1) / EF_MAX_CHUNKS;
-    if (chunk < 65536) chunk = 65536;
+    if (nchunks < 1 || nchunks > EF_MAX_CHUNKS) return EF_ERR_ARG;
+    const int64_t U = p->U, T = p->T, n = T * p->np;
+    int64_t chunk = (T + nchunks - 1) / nchunks;
     chunk = (chunk + TPB - 1) / TPB * TPB;
     const int nc = (int)((T + chunk - 1) / chunk);
     uint64_t* keys = nullptr;
-    uint32_t* cnt = nullptr;
+    uint32_t *order = nullptr, *cnt = nullptr, *wcnt = nullptr;
     void* tmp = nullptr;
+    size_t tb = radix_tmp_bytes(U);
+    if (scan_tmp_bytes(U + 1) > tb) tb = scan_tmp_bytes(U + 1);
     int st = EF_OK;
-    if (cudaMalloc((void**)&p->d_uorder, U * 4) != cudaSuccess || cudaMalloc((void**)&keys, U * 8) != cudaSuccess ||
-        cudaMalloc((void**)&cnt, EF_MAX_CHUNKS * 4) != cudaSuccess ||
-        cudaMalloc(&tmp, radix_tmp_bytes(U)) != cudaSuccess)
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    if (!ok(cudaMalloc((void**)&p->d_inv, n * 4)) || !ok(cudaMalloc((void**)&p->d_wseg, (U + 1) * 4)) ||
+        !ok(cudaMalloc((void**)&p->d_wpos_up, U * 4)) || !ok(cudaMalloc((void**)&p->d_wpos_lo, U * 4)) ||
+        !ok(cudaMalloc((void**)&order, U * 4)) || !ok(cudaMalloc((void**)&keys, U * 8)) ||
+        !ok(cudaMalloc((void**)&wcnt, U * 4)) || !ok(cudaMalloc((void**)&cnt, EF_MAX_CHUNKS * 4)) ||
+        !ok(cudaMalloc(&tmp, tb)))
         st = EF_ERR_OOM;
     uint32_t hc[EF_MAX_CHUNKS] = {0};
+    const unsigned gu = (unsigned)((U + TPB - 1) / TPB);
     if (st == EF_OK) {
         cudaMemsetAsync(cnt, 0, EF_MAX_CHUNKS * 4, s);
-        k_work_keys<<<(unsigned)((U + TPB - 1) / TPB), TPB, 0, s>>>(p->d_seg, p->d_perm, U, T, chunk, keys, p->d_uorder, cnt);
-        st = radix_sort_pairs(keys, p->d_uorder, U, bits_for(((uint64_t)(nc - 1) << 32) | 0xffffffffull), tmp, s);
-        if (st == EF_OK) cudaMemcpyAsync(hc, cnt, EF_MAX_CHUNKS * 4, cudaMemcpyDeviceToHost, s);
+        k_work_keys<<<gu, TPB, 0, s>>>(p->d_seg, p->d_perm, U, T, chunk, keys, order, cnt);
+        st = radix_sort_pairs(keys, order, U, bits_for(((uint64_t)(nc - 1) << 32) | 0xffffffffull), tmp, s);
+    }
+    if (st == EF_OK) {
+        k_work_items<<<gu, TPB, 0, s>>>(order, U, p->d_seg, p->d_pos_up, p->d_pos_lo, wcnt, p->d_wpos_up,
+                                        p->d_wpos_lo);
+        st = exclusive_scan_u32(wcnt, p->d_wseg, U, true, tmp, s);
+    }
+    if (st == EF_OK) {
+        k_work_inv<<<gu, TPB, 0, s>>>(order, U, p->d_seg, p->d_perm, p->d_wseg, p->d_inv);
+        cudaMemcpyAsync(hc, cnt, EF_MAX_CHUNKS * 4, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
-        if (st == EF_OK && e != cudaSuccess) {
-            set_last_error("build_scatter_order", e);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_last_error("build_work_order", e);
             st = EF_ERR_CUDA;
         }
     }
     cudaFree(keys);
+    cudaFree(order);
+    cudaFree(wcnt);
     cudaFree(cnt);
     cudaFree(tmp);
-    if (st != EF_OK) return st;
+    if (st != EF_OK) {
+        free_work_order(p);
+        return st;
+    }
     p->pc_chunks = nc;
     p->pc_chunk = chunk;
     p->pc_woff[0] = 0;
@@ -184,6 +259,22 @@ int build_scatter_order(ef_plan* p, cudaStream_t s)
         for (int c = 0; c <= nc; c++) EF_CUDA(cudaEventCreateWithFlags(&p->pc_ev[c], cudaEventDisableTiming));
     }
     return EF_OK;
+}
+
+int default_pipeline_chunks(const ef_plan* p)
+{
+    if (p->flags & EF_PLAN_NO_PIPELINE) return 1;
+    // enough elements per chunk for several waves of the element kernel
+    int64_t c = p->T / 393216;
+    if (c < 1) c = 1;
+    if (c > 4) c = 4;
+    return (int)c;
+}
+
+void release_work_order(ef_plan* p)
+{
+    destroy_pipeline(p);
+    free_work_order(p);
 }
 
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
@@ -200,6 +291,9 @@ int launch_pipelined(const ef_plan* p, const double* nodes, const double* coeff,
     if (p->T == 0) return EF_OK;
     const int nc = p->pc_chunks;
     if (nc <= 1) return launch_two_pass(p, nodes, coeff, K, M, s);
+    // fork: the sum stream starts after the caller's prior work
+    EF_CUDA(cudaEventRecord(p->pc_ev[nc], s));
+    EF_CUDA(cudaStreamWaitEvent(p->pc_aux, p->pc_ev[nc], 0));
     for (int c = 0; c < nc; c++) {
         const int64_t e0 = (int64_t)c * p->pc_chunk;
         const int64_t e1 = e0 + p->pc_chunk < p->T ? e0 + p->pc_chunk : p->T;
@@ -208,20 +302,10 @@ int launch_pipelined(const ef_plan* p, const double* nodes, const double* coeff,
         EF_CUDA(cudaStreamWaitEvent(p->pc_aux, p->pc_ev[c], 0));
         EF_TRY(scatter_range(p, (int64_t)p->pc_woff[c], (int64_t)p->pc_woff[c + 1], K, M, p->pc_aux));
     }
+    // join: the caller's stream waits for the last sum
     EF_CUDA(cudaEventRecord(p->pc_ev[nc], p->pc_aux));
     EF_CUDA(cudaStreamWaitEvent(s, p->pc_ev[nc], 0));
     return EF_OK;
-}
-
-void destroy_pipeline(ef_plan* p)
-{
-    if (p->pc_chunks > 1) {
-        for (int c = 0; c <= p->pc_chunks; c++)
-            if (p->pc_ev[c]) cudaEventDestroy(p->pc_ev[c]);
-        if (p->pc_aux) cudaStreamDestroy(p->pc_aux);
-    }
-    p->pc_aux = nullptr;
-    p->pc_chunks = 0;
 }
 
 }  // namespace ef

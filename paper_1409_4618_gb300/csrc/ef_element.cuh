@@ -71,6 +71,17 @@ __device__ __forceinline__ uint32_t sign_bits(const int32_t* g)
     return bits;
 }
 
+// 2x exactly: for normal x whose double stays finite, add one to the
+// exponent field on the integer pipe; otherwise (zero, subnormal, overflow,
+// inf, NaN) fall back to x + x.
+__device__ __forceinline__ double twice(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned ex = (unsigned)(b >> 52) & 0x7ffu;
+    if (ex - 1u < 0x7fdu) return __longlong_as_double(b + (1ll << 52));
+    return x + x;
+}
+
 // det H <= 0 (or NaN) marks a degenerate element; tested on the bit pattern.
 __device__ __forceinline__ bool not_positive(double x)
 {
@@ -119,7 +130,6 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     const double g11 = cM * A11, g22 = cM * A22, g33 = cM * A33, g12 = cM * A12, g13 = cM * A13, g23 = cM * A23;
     const double g01 = -(g11 + g12 + g13), g02 = -(g12 + g22 + g23), g03 = -(g13 + g23 + g33);
     const double g00 = -(g01 + g02 + g03);
-    double d;
 
     // order: (0,0)..(0,5), (1,1)..(1,5), (2,2)..(2,5), (3,3)..(3,5), (4,4),(4,5), (5,5)
     Kq[0] = k00; Kq[1] = k01; Kq[2] = k02; Kq[3] = k03; Kq[4] = k04; Kq[5] = k05;
@@ -129,27 +139,30 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     Kq[18] = h11; Kq[19] = h12;
     Kq[20] = h22;
 
-    d = g00 + g11 - g01; Mq[0] = d + d;
-    Mq[1] = fma(2.0, g12, g00 - g01 - g02);
-    Mq[2] = fma(2.0, g13, g00 - g01 - g03);
-    Mq[3] = fma(-2.0, g02, g12 - g11 + g01);
+    // shared differences: a_i = g00 - g0i, d12 = g11 - g12, d23 = g22 - g23, d31 = g33 - g13
+    const double a1 = g00 - g01, a2 = g00 - g02, a3 = g00 - g03;
+    const double d12 = g11 - g12, d23 = g22 - g23, d31 = g33 - g13;
+    Mq[0] = twice(a1 + g11);                          // 2 (g00 + g11 - g01)
+    Mq[1] = fma(2.0, g12, a1 - g02);
+    Mq[2] = fma(2.0, g13, a1 - g03);
+    Mq[3] = fma(-2.0, g02, g01 - d12);
     Mq[4] = (g13 - g12) - (g03 - g02);
-    Mq[5] = fma(2.0, g03, g11 - g13 - g01);
-    d = g00 + g22 - g02; Mq[6] = d + d;
-    Mq[7] = fma(2.0, g23, g00 - g02 - g03);
-    Mq[8] = fma(2.0, g01, g22 - g12 - g02);
-    Mq[9] = fma(-2.0, g03, g23 - g22 + g02);
+    Mq[5] = fma(2.0, g03, (g11 - g13) - g01);
+    Mq[6] = twice(a2 + g22);
+    Mq[7] = fma(2.0, g23, a2 - g03);
+    Mq[8] = fma(2.0, g01, (g22 - g12) - g02);
+    Mq[9] = fma(-2.0, g03, g02 - d23);
     Mq[10] = (g12 - g23) - (g01 - g03);
-    d = g00 + g33 - g03; Mq[11] = d + d;
+    Mq[11] = twice(a3 + g33);
     Mq[12] = (g23 - g13) - (g02 - g01);
-    Mq[13] = fma(2.0, g02, g33 - g23 - g03);
-    Mq[14] = fma(-2.0, g01, g13 - g33 + g03);
-    d = g11 + g22 - g12; Mq[15] = d + d;
-    Mq[16] = fma(-2.0, g13, g23 - g22 + g12);
-    Mq[17] = fma(-2.0, g23, g12 - g11 + g13);
-    d = g22 + g33 - g23; Mq[18] = d + d;
-    Mq[19] = fma(-2.0, g12, g13 - g33 + g23);
-    d = g33 + g11 - g13; Mq[20] = d + d;
+    Mq[13] = fma(2.0, g02, (g33 - g23) - g03);
+    Mq[14] = fma(-2.0, g01, g03 - d31);
+    Mq[15] = twice(g22 + d12);                        // 2 (g11 + g22 - g12)
+    Mq[16] = fma(-2.0, g13, g12 - d23);
+    Mq[17] = fma(-2.0, g23, g13 - d12);
+    Mq[18] = twice(g33 + d23);
+    Mq[19] = fma(-2.0, g12, g23 - d31);
+    Mq[20] = twice(g11 + d31);
 
     // signs s_k s_l on the off-diagonal pairs
     int q = 0;

@@ -68,9 +68,12 @@ inline int bits_for(uint64_t max_value)
 }  // namespace ef
 
 #define EF_MAX_CHUNKS 16
+#define EF_PLAN_NO_PIPELINE 1   // members of a batch: one chunk, no plan streams
+#define EF_PLAN_NO_ADJOINT 2    // no adjoint incidence / scratch
 
 // The plan object behind the opaque C handle.
 struct ef_plan {
+    int flags;                // EF_PLAN_* bits
     int kind, dim, variant;
     int nv;     // nodes per element
     int nl;     // local DOFs
@@ -86,10 +89,14 @@ struct ef_plan {
     int32_t* d_colidx;    // nnz
     uint32_t* d_seg;      // U + 1: contribution range of each upper nonzero
     uint32_t* d_perm;     // T * np: local-matrix index (pair * T + elem) of each contribution, segment order
+    uint32_t* d_inv;      // T * np: position of (pair * T + elem) in the work-ordered contribution list
     uint32_t* d_pos_up;   // U: CSR position of (r, c), r <= c
     uint32_t* d_pos_lo;   // U: CSR position of (c, r), or 0xffffffff on the diagonal
-    uint32_t* d_uorder;   // U: work order of the sum (completing chunk, then count inside 256-windows)
-    double* d_local;      // 2 * np * T: scratch for the two-pass path (K pairs then M pairs)
+    uint32_t* d_wseg;     // U + 1: list range of each work item of the sum (work order: completing
+                          //   chunk, then descending contribution count inside 256-windows of u)
+    uint32_t* d_wpos_up;  // U: CSR position of (r, c) of each work item
+    uint32_t* d_wpos_lo;  // U: CSR position of (c, r), or 0xffffffff
+    double* d_local;      // 2 * np * T: contribution list (K then M values) of the two-pass paths
     int* d_status;        // device status word
 
     // fused path (blocks of fb_block consecutive elements): see ef_fused.cu
@@ -115,8 +122,8 @@ struct ef_plan {
     int pc_chunks;                       // number of element chunks (<= 1: not pipelined)
     int64_t pc_chunk;                    // elements per chunk
     uint32_t pc_woff[EF_MAX_CHUNKS + 1]; // work-list range of the sums each chunk completes
-    cudaStream_t pc_aux;
-    cudaEvent_t pc_ev[EF_MAX_CHUNKS + 1];
+    cudaStream_t pc_aux;                 // sums
+    cudaEvent_t pc_ev[EF_MAX_CHUNKS + 2];
     int use_blocked;                     // ef_assemble runs the element-block kernel (ef_plan_set_block)
 
     // host staging for ef_assemble_host
@@ -125,11 +132,15 @@ struct ef_plan {
 
 namespace ef {
 const char* last_error_text();
+int plan_create_internal(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, cudaStream_t s,
+                         int flags, ef_plan** out);
 int validate_elems(ef_plan* p, cudaStream_t s);
 int build_topology(ef_plan* p, cudaStream_t s);
 int build_pattern(ef_plan* p, cudaStream_t s);
 int build_fused(ef_plan* p, cudaStream_t s);
-int build_scatter_order(ef_plan* p, cudaStream_t s);
+int build_work_order(ef_plan* p, int nchunks, cudaStream_t s);
+int default_pipeline_chunks(const ef_plan* p);
+void release_work_order(ef_plan* p);
 // Order a list of upper nonzeros by descending contribution count (stable), in place.
 int order_by_count(const uint32_t* seg, uint32_t* list, int64_t n, uint64_t* keys, uint32_t* vals, void* tmp,
                    cudaStream_t s);

@@ -53,6 +53,14 @@ class PlanInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchConfig(C.Structure):
+    _fields_ = [("elems_per_tile", C.c_int32), ("sum_tile", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("dynamic", C.c_int32), ("largest_first", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class _CSR(C.Structure):
     _fields_ = [("n_dofs", C.c_int64), ("nnz", C.c_int64), ("d_rowptr", C.c_void_p), ("d_colidx", C.c_void_p),
                 ("d_K", C.c_void_p), ("d_M", C.c_void_p)]
@@ -80,6 +88,8 @@ def load():
             "ef_plan_pattern": ([P, P, P, P], I),
             "ef_plan_info": ([P, C.POINTER(PlanInfo)], I),
             "ef_plan_set_block": ([P, I, P], I),
+            "ef_plan_set_pipeline": ([P, I, P], I),
+            "ef_plan_tune": ([P, P, P, P, P, I, C.POINTER(C.c_int), P], I),
             "ef_plan_topology": ([P, P, P, P, P], I),
             "ef_assemble": ([P, P, P, P, P, P], I),
             "ef_assemble_two_pass": ([P, P, P, P, P, P], I),
@@ -91,6 +101,16 @@ def load():
             "rt0_assemble": ([I, P, I64, P, I64, P, C.POINTER(_CSR), P], I),
             "ned_assemble": ([I, P, I64, P, I64, P, C.POINTER(_CSR), P], I),
             "ef_csr_free": ([C.POINTER(_CSR)], None),
+            "ef_batch_create": ([I, I, I, P, P, P, P, C.POINTER(P)], I),
+            "ef_batch_sizes": ([P, P, P], I),
+            "ef_batch_pattern": ([P, I, P, P, P], I),
+            "ef_batch_bind": ([P, P, P, P, P, P], I),
+            "ef_batch_assemble": ([P, P], I),
+            "ef_batch_tune": ([P, I, C.POINTER(BatchConfig), P], I),
+            "ef_batch_get_config": ([P, C.POINTER(BatchConfig)], I),
+            "ef_batch_set_config": ([P, C.POINTER(BatchConfig), P], I),
+            "ef_batch_check": ([P, P], I),
+            "ef_batch_destroy": ([P], None),
             "ef_status_string": ([I], C.c_char_p),
             "ef_last_error": ([], C.c_char_p),
         }
@@ -260,6 +280,18 @@ class Plan:
     def set_block(self, block: int, stream=None):
         ef_plan_set_block(self.handle, block, stream)
 
+    def set_pipeline(self, chunks: int, stream=None):
+        _check(load().ef_plan_set_pipeline(self.handle, int(chunks), _stream_ptr(stream)))
+
+    def tune(self, nodes, coeff=None, K=None, M=None, reps: int = 5, stream=None) -> int:
+        """Pick the fastest ef_assemble schedule for this plan; returns chunks (or -block)."""
+        K, M = self._vals(K, M)
+        chosen = C.c_int(0)
+        _check(load().ef_plan_tune(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
+                                   _dev(K, torch.float64, "K"), _dev(M, torch.float64, "M"), int(reps),
+                                   C.byref(chosen), _stream_ptr(stream)))
+        return chosen.value
+
     def pattern(self, stream=None):
         rowptr = torch.empty(self.n_dofs + 1, dtype=torch.int64, device=self.device)
         colidx = torch.empty(max(self.nnz, 0), dtype=torch.int32, device=self.device)
@@ -313,6 +345,82 @@ class Plan:
     def close(self):
         if self._h is not None:
             ef_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_array(tensors, dtype, name, allow_none=False):
+    out = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        if t is None:
+            if not allow_none:
+                raise TypeError(f"{name}[{i}] is None")
+            out[i] = None
+        else:
+            out[i] = _dev(t, dtype, f"{name}[{i}]")
+    return out
+
+
+class Batch:
+    """Many independent meshes assembled by one persistent launch (ef_batch_*)."""
+
+    def __init__(self, kind: int, dim: int, n_nodes, elems, stream=None):
+        lib = load()
+        self.kind, self.dim, self.n = kind, dim, len(elems)
+        self.device = elems[0].device
+        nn = (C.c_int64 * self.n)(*[int(v) for v in n_nodes])
+        ne = (C.c_int64 * self.n)(*[int(e.shape[0]) for e in elems])
+        ep = _ptr_array(elems, torch.int32, "elems")
+        self._h = C.c_void_p()
+        _check(lib.ef_batch_create(kind, dim, self.n, nn, ne, ep, _stream_ptr(stream), C.byref(self._h)))
+        nd = (C.c_int64 * self.n)()
+        nz = (C.c_int64 * self.n)()
+        _check(lib.ef_batch_sizes(self._h, nd, nz))
+        self.n_dofs, self.nnz = list(nd), list(nz)
+        self.n_elems = [int(e.shape[0]) for e in elems]
+
+    def pattern(self, mesh: int, stream=None):
+        rowptr = torch.empty(self.n_dofs[mesh] + 1, dtype=torch.int64, device=self.device)
+        colidx = torch.empty(self.nnz[mesh], dtype=torch.int32, device=self.device)
+        _check(load().ef_batch_pattern(self._h, mesh, _dev(rowptr, torch.int64, "rowptr"),
+                                       _dev(colidx, torch.int32, "colidx"), _stream_ptr(stream)))
+        return rowptr, colidx
+
+    def bind(self, nodes, coeff, K, M, stream=None):
+        self._bound = (list(nodes), None if coeff is None else list(coeff), list(K), list(M))  # keep alive
+        cp = None if coeff is None else _ptr_array(coeff, torch.float64, "coeff", allow_none=True)
+        _check(load().ef_batch_bind(self._h, _ptr_array(nodes, torch.float64, "nodes"), cp,
+                                    _ptr_array(K, torch.float64, "K"), _ptr_array(M, torch.float64, "M"),
+                                    _stream_ptr(stream)))
+
+    def assemble(self, stream=None):
+        _check(load().ef_batch_assemble(self._h, _stream_ptr(stream)))
+
+    def tune(self, reps: int = 3, stream=None) -> dict:
+        cfg = BatchConfig()
+        _check(load().ef_batch_tune(self._h, reps, C.byref(cfg), _stream_ptr(stream)))
+        return cfg.as_dict()
+
+    def config(self) -> dict:
+        cfg = BatchConfig()
+        _check(load().ef_batch_get_config(self._h, C.byref(cfg)))
+        return cfg.as_dict()
+
+    def set_config(self, stream=None, **kw):
+        cfg = BatchConfig(**{**self.config(), **kw})
+        _check(load().ef_batch_set_config(self._h, C.byref(cfg), _stream_ptr(stream)))
+
+    def check(self, stream=None):
+        _check(load().ef_batch_check(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value is not None:
+            load().ef_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -51,6 +51,9 @@ def run_gpu(kind, dim, nodes, elems, coeff=None, path="default", check=True):
         elif path.startswith("blocked"):
             plan.set_block(int(path[len("blocked"):]))
             K, M = plan.assemble(tn, tc)
+        elif path.startswith("chunks"):
+            plan.set_pipeline(int(path[len("chunks"):]))
+            K, M = plan.assemble(tn, tc)
         else:
             K, M = plan.assemble(tn, tc)
         if check:

@@ -93,12 +93,11 @@ def test_paths_agree_bitwise_and_runs_repeat(ora, kind):
     run after run; and the pipelined result passes parity."""
     nodes, elems = mg.kuhn_cube(28, 0.2, 12)
     coeff = mg.log_uniform_coeff(12, elems.shape[0])
-    a = run_gpu(kind, 3, nodes, elems, coeff, path="default")
-    b = run_gpu(kind, 3, nodes, elems, coeff, path="two_pass")
-    c = run_gpu(kind, 3, nodes, elems, coeff, path="default")
-    d = run_gpu(kind, 3, nodes, elems, coeff, path="blocked128")
+    a = run_gpu(kind, 3, nodes, elems, coeff, path="chunks3")
+    others = [run_gpu(kind, 3, nodes, elems, coeff, path=p)
+              for p in ("default", "two_pass", "chunks3", "chunks16", "blocked128", "blocked256")]
     for key in ("K", "M"):
-        for other in (b, c, d):
+        for other in others:
             assert np.array_equal(a[key].view(np.uint64), other[key].view(np.uint64))
     compare(a, ora.assemble(kind, 3, nodes, elems, coeff))
 
@@ -142,6 +141,25 @@ def test_one_shot_and_host_path_match_plan(ora):
     o = ora.assemble(RT0, 2, *mg.kuhn_square(5))
     np.testing.assert_array_equal(rt["colidx"].cpu().numpy(), o["colidx"])
     assert np.abs(rt["K"].cpu().numpy() - o["K"]).max() <= 1e-12 * np.abs(o["K"]).max()
+
+
+def test_tuner_keeps_results_and_picks_a_schedule():
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(36, 0.2, 14)           # 279,936 tets: pipelines up to 4 chunks are tried
+    coeff = mg.log_uniform_coeff(14, elems.shape[0])
+    tn, tc = torch.from_numpy(nodes).cuda(), torch.from_numpy(coeff).cuda()
+    plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).cuda())
+    K0, M0 = plan.assemble_two_pass(tn, tc)
+    chosen = plan.tune(tn, tc, reps=2)
+    assert chosen in (1, 2, 3, 4, -128, -256)
+    K, M = plan.assemble(tn, tc)
+    torch.cuda.synchronize()
+    assert torch.equal(K.view(torch.int64), K0.view(torch.int64))
+    assert torch.equal(M.view(torch.int64), M0.view(torch.int64))
+    plan.close()
 
 
 def test_errors_are_reported():
@@ -188,7 +206,8 @@ def test_cuda_graph_capture_replays_bitwise():
     coeff = mg.log_uniform_coeff(13, elems.shape[0])
     tn, tc = torch.from_numpy(nodes).cuda(), torch.from_numpy(coeff).cuda()
     plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).cuda())
-    assert plan.info()["pipeline_chunks"] > 1
+    plan.set_pipeline(3)
+    assert plan.info()["pipeline_chunks"] == 3
     K0, M0 = plan.assemble(tn, tc)
     K = torch.zeros_like(K0)
     M = torch.zeros_like(M0)
