@@ -9,8 +9,10 @@ jittered by +-0.2h (seed 2), per-element coefficient log-uniform in
 shape-optimisation loop where only coordinates and coefficients change.
 
 Prints one JSON line: throughput (M elements / s), e2e through the host-buffer
-C-ABI call, the HBM and FP64 rooflines of the step's kernel(s), the clocks
-seen while timing, and the CPU oracle timed on this host.
+C-ABI call, the roofline of the step's dominant kernel (timed per launch by
+CUDA events the library records on the launching stream inside the timed
+region), the HBM fraction of the whole step, the clocks seen while timing,
+and the CPU oracle timed on this host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -39,8 +41,16 @@ from paper_1409_4618_gb300 import meshgen as mg  # noqa: E402
 WORKLOAD = {"name": "ned3d_kuhn64_jitter0.2", "kind": 2, "dim": 3, "n": 64, "jitter": 0.2, "seed": 2}
 METRIC = "M elements/s assembled to CSR (K+M), % HBM roofline; batched & adjoint vs plain"
 UNIT = "Melem/s"
-FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (non-tensor) nominal, FMA = 2 flops
+# FP64 pipe peak: 152 SMs x 2 FP64 results per clock per SM x 2070 MHz (the
+# GB300's 1.25 TFLOP/s FP64 with FMA = 2 flops); DADD, DMUL, DFMA count 1 op.
+SMS, FP64_PER_CLK_PER_SM, SM_MAX_MHZ = 152, 2, 2070
+FP64_PEAK_TOPS = SMS * FP64_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes (read + write) per element of the Nedelec-3D element kernel of
+# the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
+# on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
+# to the elements.
+ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (166.109952e6 + 253.171968e6) / 663552
 
 
 def _peaks():
@@ -49,6 +59,17 @@ def _peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _nvtx(torch, name):
+    """Mark the timed region as an NVTX range (a profiler can filter on it)."""
+    try:
+        if name:
+            torch.cuda.nvtx.range_push(name)
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
 
 
 def _workload():
@@ -304,21 +325,28 @@ def run_gpu(args):
     plan.check()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, device time by CUDA events on the launching stream
+    # ---- timed region: K steps, device time by CUDA events on the launching stream;
+    # the library records its own per-kernel events on that stream for the same K calls
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if path != "two_pass":
+        plan.profile(args.steps)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        _nvtx(torch, "timed")
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        _nvtx(torch, None)
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     plan.check()
+    k_first, k_second, k_calls = plan.profile_read() if path != "two_pass" else (0.0, 0.0, 0)
+    plan.profile(0)
     ms_t = torch.tensor([ms], device=dev)
     if dist:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -345,23 +373,44 @@ def run_gpu(args):
            "h2d_bytes_per_step": int(hn.numel() * 8 + hc.numel() * 8),
            "d2h_bytes_per_step": int(2 * nnz * 8)}
 
-    # ---- rooflines of the step
+    # ---- rooflines: the dominant kernel (per-launch CUDA events), and HBM for the whole step
     peaks, src = _peaks()
     alg_bytes = 16 * T + 8 * T + 8 * w["dim"] * V + 16 * nnz
     achieved_gbs = alg_bytes / (ms_step / 1e3) / 1e9
-    n_pairs = 21
-    U = (nnz + plan.n_dofs) // 2
-    fp64_ops = T * fp64_ops_per_element(w["kind"], w["dim"]) + 2 * (T * n_pairs - U)
-    achieved_ops = fp64_ops / (ms_step / 1e3) / 1e12
-    fp64_peak_ops = FP64_NOMINAL_TFLOPS / 2.0    # T FP64 pipe ops / s (one DFMA = 2 flops)
+    info = plan.info()
+    U = info["n_upper"]
+    n_pairs = info["n_contrib"] // T
+    elem_ops = T * fp64_ops_per_element(w["kind"], w["dim"])
+    sum_ops = 2 * (T * n_pairs - U)
+    sum_bytes = 2 * n_pairs * 8 * T + 12 * U + 16 * nnz
+    if k_calls > 0 and info["fused_block"] == 0 and info["assemble_launches"] == 2:
+        ms_e, ms_s = k_first / k_calls, k_second / k_calls
+        kernels = {"element": {"ms_per_launch": ms_e, "share": ms_e / (ms_e + ms_s)},
+                   "sum": {"ms_per_launch": ms_s, "share": ms_s / (ms_e + ms_s),
+                           "achieved_gbs": sum_bytes / (ms_s / 1e3) / 1e9,
+                           "frac_hbm": sum_bytes / (ms_s / 1e3) / 1e9 / peaks["hbm_gbs"],
+                           "algorithmic_bytes": int(sum_bytes)}}
+        dom_name, dom_ms, dom_ops = "k_element_local (two-pass element kernel)", ms_e, elem_ops
+        traffic = (None if ELEMENT_KERNEL_DRAM_BYTES_PER_TET is None
+                   else ELEMENT_KERNEL_DRAM_BYTES_PER_TET * T)
+    else:
+        one = k_first / k_calls if k_calls else ms_step
+        kernels = {"step": {"ms_per_launch": one}}
+        dom_name, dom_ms, dom_ops, traffic = "ef_assemble (" + path + ")", one if k_calls else ms_step, \
+            elem_ops + sum_ops, None
+    achieved_ops = dom_ops / (dom_ms / 1e3) / 1e12
     roofline = {
-        "bound": "alu", "unit": "T fp64-ops/s", "achieved": achieved_ops, "peak": fp64_peak_ops,
-        "frac": achieved_ops / fp64_peak_ops, "traffic": None,
-        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s / 2 (DADD, DMUL, DFMA = 1 op each)",
-        "kernel": "ef_assemble step (" + path + ")",
-        "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved_gbs / peaks["hbm_gbs"], "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_step": int(alg_bytes), "bytes_per_elem": alg_bytes / T},
+        "bound": "alu", "unit": "T fp64-ops/s", "achieved": achieved_ops, "peak": FP64_PEAK_TOPS,
+        "frac": achieved_ops / FP64_PEAK_TOPS, "traffic": traffic,
+        "peak_source": f"{SMS} SMs x {FP64_PER_CLK_PER_SM} FP64 ops/clk/SM x {SM_MAX_MHZ} MHz "
+                       "(DADD, DMUL, DFMA = 1 op each)",
+        "kernel": dom_name, "ms_per_launch": dom_ms,
+        "fp64_ops_per_launch": int(dom_ops), "fp64_ops_per_elem": dom_ops / T,
+        "kernels": kernels,
+        "hbm_step": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved_gbs / peaks["hbm_gbs"],
+                     "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_step": int(alg_bytes), "bytes_per_elem": alg_bytes / T},
     }
     info = plan.info()
     launches = (2 if path == "two_pass" else info["assemble_launches"]) * args.steps
@@ -401,9 +450,15 @@ def main():
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--adjoint-steps", type=int, default=50)
+    ap.add_argument("--cube", type=int, default=64,
+                    help="cubes per axis of the single-mesh workload (smaller values: profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.cube != WORKLOAD["n"]:
+        if args.cube < 4:
+            ap.error("--cube must be >= 4")
+        WORKLOAD.update(n=args.cube, name=f"ned3d_kuhn{args.cube}_jitter0.2")
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -98,12 +98,13 @@ typedef struct {
     int32_t fused_block;          /* elements per CTA of the element-block path if selected, else 0 */
     int64_t fused_blocks;
     int64_t fused_partial;        /* element-block path: contributions summed by the fix-up */
-    int32_t pipeline_chunks;      /* element chunks of the pipelined path (1: plain two-pass order) */
+    int32_t pipeline_chunks;      /* element chunks of the work order (the persistent queue's chunks) */
 } ef_plan_info_t;
 int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info);
 
-/* Select how ef_assemble runs. block = 0: the pipelined two-pass path
- * (default). block = 128 or 256: the element-block path, one CTA per block of
+/* Select how ef_assemble runs. block = 0: leave the element-block path
+ * (back to the two-pass kernels or the queue selected before). block = 128
+ * or 256: the element-block path, one CTA per block of
  * `block` elements that keeps its local matrices in shared memory, completes
  * the nonzeros lying wholly in the block and hands the others to a fix-up
  * kernel. Results are identical bit for bit (same summation order); only
@@ -111,18 +112,34 @@ int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info);
  * block schedule. Errors: EF_ERR_ARG, EF_ERR_OOM. */
 int ef_plan_set_block(ef_plan* plan, int block, void* stream);
 
-/* Select the pipelined path with `chunks` element chunks (1 = the plain
- * two-pass order on one stream, up to 16). Results do not depend on it.
- * Synchronises `stream`; reallocates the plan's work-order arrays. */
+/* Select the one-launch persistent queue with `chunks` element chunks (1 to
+ * 16; sums of a chunk may start once the chunks they depend on are done).
+ * Results do not depend on it. Synchronises `stream`; reallocates the plan's
+ * work-order arrays. */
 int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream);
 
 /* Autotuner for ef_assemble on this plan: times `reps` calls of each
- * candidate (pipelines of 1, 2, 3, 4, 6, 8 chunks of at least 64K elements;
- * element-block path with 128 or 256 elements per CTA) on the given buffers,
- * keeps the fastest and reports it in *chosen (chunks, or -block) if not
- * NULL. Overwrites d_Kval / d_Mval. Synchronises `stream`. */
+ * candidate on the given buffers and keeps the fastest: the plain two-pass
+ * kernels (*chosen = 0); the one-launch persistent queue with 4, 8 or 16
+ * element chunks, 128 or 256 elements per tile, 1024 or 4096 nonzeros per
+ * sum tile and 0, 1 or 2 element-only CTAs per four (*chosen = chunks*100 +
+ * elem_ctas*10 + (tile == 256)); the element-block path (*chosen = -block).
+ * Overwrites d_Kval / d_Mval. Synchronises `stream`. */
 int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
                  int reps, int* chosen, void* stream);
+
+/* Device time per kernel of ef_assemble. ef_plan_profile(plan, n) creates
+ * 3n CUDA events and records them, on each call's stream, around the kernels
+ * of the next n ef_assemble calls on this plan: before the first kernel,
+ * between the first and the second, after the last (n = 0 stops recording
+ * and frees the events). ef_plan_profile_read waits for the recorded events
+ * and returns the summed milliseconds of the first kernel (the element kernel
+ * of the two-pass schedule, the fused kernel of the element-block one, the
+ * whole launch of the persistent queue) and of the second (the sum, the
+ * fix-up, 0), and the number of calls recorded. Either output may be NULL.
+ * Errors: EF_ERR_ARG, EF_ERR_CUDA. */
+int ef_plan_profile(ef_plan* plan, int max_calls);
+int ef_plan_profile_read(const ef_plan* plan, double* ms_first, double* ms_second, int* calls);
 
 /* Copy the CSR pattern into caller buffers: d_rowptr [n_dofs+1] int64,
  * d_colidx [nnz] int32 (device). Asynchronous on `stream`. */
@@ -140,11 +157,9 @@ int ef_plan_topology(const ef_plan* plan, int32_t* d_elem2dof, uint8_t* d_signbi
  * Assemble K and M values into caller-owned CSR value arrays (pattern of
  * ef_plan_pattern): local matrices by the closed forms of the Sec. 2.4
  * integrals on every element, then the fixed-order sum into each nonzero.
- * With more than one pipeline chunk (ef_plan_set_pipeline, ef_plan_tune),
- * the element kernel runs in chunks on `stream` and the sums of the nonzeros
- * a chunk completes run on a plan-owned stream while the next chunk computes
- * (joined back into `stream` by events, so the call is one unit of work on
- * `stream` and captures into a CUDA graph as a fork/join).
+ * By default two kernels (those of ef_assemble_two_pass); ef_plan_tune,
+ * ef_plan_set_pipeline and ef_plan_set_block select another schedule (one
+ * persistent launch, or the element-block kernels) with the same values.
  *   d_nodes: n_nodes x dim doubles; d_coeff: n_elems doubles or NULL (= 1);
  *   d_Kval, d_Mval: nnz doubles each (overwritten).
  * Asynchronous; allocates nothing; no host synchronisation (capturable in a
@@ -230,10 +245,10 @@ int ef_adjoint(const ef_plan* plan, const double* d_nodes, const double* d_coeff
 /*
  * A batch holds independent meshes of one kind and dimension, each with its
  * own plan and its own CSR. ef_batch_assemble assembles all of them in ONE
- * persistent kernel launch: a queue hands out every (mesh, element tile)
- * before any (mesh, sum tile); a sum tile starts once its mesh's element
- * tiles are done (a bounded wait; EF_ERR_TIMEOUT from ef_batch_check if a
- * wait gave up). Values are those of ef_assemble on each mesh, bit for bit.
+ * persistent kernel launch over (mesh, element tile) and (mesh, sum tile)
+ * work; a sum tile starts once the element tiles it depends on are done (a
+ * bounded wait; EF_ERR_TIMEOUT from ef_batch_check if a wait gave up). Values
+ * are those of ef_assemble on each mesh, bit for bit.
  */
 typedef struct ef_batch ef_batch;
 
@@ -244,6 +259,9 @@ typedef struct {
     int32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x number of SMs */
     int32_t dynamic;         /* 1: tiles by an integer ticket; 0: static stride blockIdx + k gridDim */
     int32_t largest_first;   /* 1: meshes in order of decreasing size; 0: as given */
+    int32_t elem_ctas;       /* 0: every CTA takes tiles of both kinds from one interleaved queue;
+                                k in 1..3: in each group of 4 CTAs, k take only element tiles and
+                                4-k only sum tiles (two queues) */
 } ef_batch_config_t;
 
 /* Build the per-mesh plans (as ef_plan_create for each). n_nodes, n_elems:

@@ -3,7 +3,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "ef_internal.cuh"
+#include "ef_queue.cuh"
 
 using namespace ef;
 
@@ -75,10 +78,13 @@ int create(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d
             break;
         }
         if ((st = build_work_order(p, default_pipeline_chunks(p), s)) != EF_OK) break;
+        if (!(flags & EF_PLAN_NO_PIPELINE) && (st = plan_queue_rebuild(p, s)) != EF_OK) break;
         if (!(flags & EF_PLAN_NO_ADJOINT) && (st = build_adjoint(p, s)) != EF_OK) break;
+        p->use_two_pass = 1;   // the fastest schedule until ef_plan_tune / ef_plan_set_pipeline picks another
     } while (0);
     if (st != EF_OK) {
         cudaStreamSynchronize(s);
+        plan_queue_free(p);
         release_work_order(p);
         free_plan_memory(p);
         free(p);
@@ -102,7 +108,10 @@ int one_shot(int kind, int dim, const double* d_nodes, int64_t n_nodes, const in
     memset(out, 0, sizeof(*out));
     if (n_elems > 0 && !d_nodes) return EF_ERR_ARG;
     ef_plan* p = nullptr;
-    int st = ef_plan_create(kind, dim, n_nodes, n_elems, d_elems, stream, &p);
+    int st = plan_args(kind, dim, n_nodes, n_elems, d_elems);
+    if (st == EF_OK)
+        st = create(kind, dim, n_nodes, n_elems, d_elems, (cudaStream_t)stream,
+                    EF_PLAN_NO_PIPELINE | EF_PLAN_NO_ADJOINT, &p);
     if (st != EF_OK) return st;
     ef_csr c;
     memset(&c, 0, sizeof(c));
@@ -131,6 +140,51 @@ int one_shot(int kind, int dim, const double* d_nodes, int64_t n_nodes, const in
 }  // namespace
 
 namespace ef {
+
+// CUDA events of ef_plan_profile: three per recorded ef_assemble call.
+struct Profile {
+    std::vector<cudaEvent_t> ev;
+    std::vector<char> two;   // per call: a second kernel ran between the middle and last events
+    int cap = 0, calls = 0;
+    bool mid = false;
+};
+
+void profile_begin(const ef_plan* p, cudaStream_t s)
+{
+    Profile* pr = p->prof;
+    if (!pr || pr->calls >= pr->cap) return;
+    cudaEventRecord(pr->ev[(size_t)3 * pr->calls], s);
+    pr->mid = false;
+}
+
+void profile_mid(const ef_plan* p, cudaStream_t s)
+{
+    Profile* pr = p->prof;
+    if (!pr || pr->calls >= pr->cap) return;
+    cudaEventRecord(pr->ev[(size_t)3 * pr->calls + 1], s);
+    pr->mid = true;
+}
+
+void profile_end(const ef_plan* p, cudaStream_t s)
+{
+    Profile* pr = p->prof;
+    if (!pr || pr->calls >= pr->cap) return;
+    cudaEvent_t* e = &pr->ev[(size_t)3 * pr->calls];
+    if (!pr->mid) cudaEventRecord(e[1], s);   // one-kernel paths: all time is the first kernel's
+    cudaEventRecord(e[2], s);
+    pr->two[pr->calls] = pr->mid ? 1 : 0;
+    pr->calls++;
+}
+
+void profile_free(ef_plan* p)
+{
+    if (!p->prof) return;
+    for (cudaEvent_t e : p->prof->ev)
+        if (e) cudaEventDestroy(e);
+    delete p->prof;
+    p->prof = nullptr;
+}
+
 int plan_create_internal(int kind, int dim, int64_t n_nodes, int64_t n_elems, const int32_t* d_elems, cudaStream_t s,
                          int flags, ef_plan** out)
 {
@@ -175,7 +229,7 @@ int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info)
     else if (plan->use_blocked && plan->fb_nblocks > 0)
         info->assemble_launches = plan->n_px > 0 ? 2 : 1;
     else
-        info->assemble_launches = plan->pc_chunks > 1 ? 2 * plan->pc_chunks : 2;
+        info->assemble_launches = (plan->queue && !plan->use_two_pass) ? 1 : 2;
     info->fused_block = plan->use_blocked ? plan->fb_block : 0;
     info->pipeline_chunks = plan->pc_chunks;
     info->fused_blocks = plan->fb_nblocks;
@@ -193,6 +247,7 @@ int ef_plan_set_block(ef_plan* plan, int block, void* stream)
     if (!fused_block_supported(block)) return EF_ERR_ARG;
     EF_TRY(build_fused_block(plan, block, (cudaStream_t)stream));
     plan->use_blocked = 1;
+    plan->use_two_pass = 0;
     return EF_OK;
 }
 
@@ -201,7 +256,9 @@ int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream)
     if (!plan || chunks < 1 || chunks > EF_MAX_CHUNKS) return EF_ERR_ARG;
     if (plan->flags & EF_PLAN_NO_PIPELINE) return EF_ERR_ARG;
     EF_TRY(build_work_order(plan, chunks, (cudaStream_t)stream));
+    EF_TRY(plan_queue_rebuild(plan, (cudaStream_t)stream));
     plan->use_blocked = 0;
+    plan->use_two_pass = 0;
     return EF_OK;
 }
 
@@ -215,16 +272,55 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
     cudaEvent_t e0, e1;
     EF_CUDA(cudaEventCreate(&e0));
     EF_CUDA(cudaEventCreate(&e1));
-    // candidates: pipelines of 1..8 chunks (chunks of at least 64K elements), element-block 128 / 256
-    const int cand[] = {1, 2, 3, 4, 6, 8, -128, -256};
-    int best = 1, st = EF_OK;
+    struct Cand {
+        int chunks, block, two_pass;   // block > 0: element-block path; two_pass: plain kernels
+        ef_batch_config_t q;
+    };
+    std::vector<Cand> cands;
+    {
+        Cand k{};
+        k.two_pass = 1;
+        k.chunks = 1;
+        cands.push_back(k);
+    }
+    const int chunk_opts[] = {4, 8, 16};
+    for (int c : chunk_opts) {
+        if (c > 1 && plan->T / c < 8192) continue;
+        for (int be : {128, 256})
+            for (int bu : {1024, 4096})
+                for (int ec : {0, 1, 2}) {
+                    Cand k{};
+                    k.chunks = c;
+                    k.q.elems_per_tile = be;
+                    k.q.sum_tile = bu;
+                    k.q.dynamic = 1;
+                    k.q.largest_first = 0;
+                    k.q.elem_ctas = ec;
+                    k.q.ctas_per_sm = queue_max_ctas_per_sm(plan->variant, be);
+                    if (ec > 0) k.q.ctas_per_sm = (k.q.ctas_per_sm / 4) * 4;   // whole groups of four
+                    if (k.q.ctas_per_sm >= 1) cands.push_back(k);
+                }
+    }
+    for (int b : {128, 256}) {
+        Cand k{};
+        k.block = b;
+        cands.push_back(k);
+    }
+    int st = EF_OK, best = -1;
     float best_ms = 1e30f;
-    for (int c : cand) {
-        if (c > 1 && plan->T / c < 65536) continue;
-        if (c > 0)
-            st = ef_plan_set_pipeline(plan, c, stream);
-        else
-            st = ef_plan_set_block(plan, -c, stream);
+    for (size_t i = 0; i < cands.size() && st == EF_OK; i++) {
+        const Cand& c = cands[i];
+        if (c.block > 0)
+            st = ef_plan_set_block(plan, c.block, stream);
+        else if (c.two_pass) {
+            if (plan->pc_chunks != 1) st = ef_plan_set_pipeline(plan, 1, stream);
+            plan->use_two_pass = 1;
+        } else {
+            if (plan->pc_chunks != c.chunks) st = ef_plan_set_pipeline(plan, c.chunks, stream);
+            plan->use_blocked = 0;
+            plan->use_two_pass = 0;
+            if (st == EF_OK) st = plan_queue_config(plan, c.q, s);
+        }
         if (st != EF_OK) break;
         if ((st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream)) != EF_OK) break;
         cudaEventRecord(e0, s);
@@ -238,14 +334,26 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best_ms) {
             best_ms = ms;
-            best = c;
+            best = (int)i;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st != EF_OK) return st;
-    st = best > 0 ? ef_plan_set_pipeline(plan, best, stream) : ef_plan_set_block(plan, -best, stream);
-    if (st == EF_OK && chosen) *chosen = best;
+    if (st != EF_OK || best < 0) return st != EF_OK ? st : EF_ERR_ARG;
+    const Cand& c = cands[best];
+    if (c.block > 0) {
+        st = ef_plan_set_block(plan, c.block, stream);
+        if (chosen) *chosen = -c.block;
+    } else if (c.two_pass) {
+        st = ef_plan_set_pipeline(plan, 1, stream);
+        plan->use_two_pass = 1;
+        if (chosen) *chosen = 0;
+    } else {
+        st = ef_plan_set_pipeline(plan, c.chunks, stream);
+        plan->use_blocked = 0;
+        if (st == EF_OK) st = plan_queue_config(plan, c.q, s);
+        if (chosen) *chosen = c.chunks * 100 + c.q.elem_ctas * 10 + (c.q.elems_per_tile == 256);
+    }
     return st == EF_OK ? ef_plan_check(plan, stream) : st;
 }
 
@@ -286,8 +394,62 @@ int ef_assemble(const ef_plan* plan, const double* d_nodes, const double* d_coef
 {
     EF_TRY(assemble_checks(plan, d_nodes, d_Kval, d_Mval));
     cudaStream_t s = (cudaStream_t)stream;
-    if (plan->use_blocked && plan->fb_nblocks > 0) return launch_fused(plan, d_nodes, d_coeff, d_Kval, d_Mval, s);
-    return launch_pipelined(plan, d_nodes, d_coeff, d_Kval, d_Mval, s);
+    profile_begin(plan, s);
+    int st;
+    if (plan->use_blocked && plan->fb_nblocks > 0)
+        st = launch_fused(plan, d_nodes, d_coeff, d_Kval, d_Mval, s);
+    else if (!plan->queue || plan->use_two_pass)
+        st = launch_two_pass(plan, d_nodes, d_coeff, d_Kval, d_Mval, s);
+    else
+        st = launch_queue(plan, d_nodes, d_coeff, d_Kval, d_Mval, s);
+    profile_end(plan, s);
+    return st;
+}
+
+int ef_plan_profile(ef_plan* plan, int max_calls)
+{
+    if (!plan || max_calls < 0) return EF_ERR_ARG;
+    profile_free(plan);
+    if (max_calls == 0) return EF_OK;
+    Profile* pr = new Profile();
+    pr->cap = max_calls;
+    pr->ev.assign((size_t)3 * max_calls, nullptr);
+    pr->two.assign((size_t)max_calls, 0);
+    for (cudaEvent_t& e : pr->ev) {
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) {
+            set_last_error("cudaEventCreate", r);
+            plan->prof = pr;
+            profile_free(plan);
+            return EF_ERR_CUDA;
+        }
+    }
+    plan->prof = pr;
+    return EF_OK;
+}
+
+int ef_plan_profile_read(const ef_plan* plan, double* ms_first, double* ms_second, int* calls)
+{
+    if (!plan) return EF_ERR_ARG;
+    double a = 0, b = 0;
+    int n = 0;
+    if (plan->prof) {
+        Profile* pr = plan->prof;
+        n = pr->calls;
+        for (int c = 0; c < n; c++) {
+            cudaEvent_t* e = &pr->ev[(size_t)3 * c];
+            EF_CUDA(cudaEventSynchronize(e[2]));
+            float x = 0, y = 0;
+            EF_CUDA(cudaEventElapsedTime(&x, e[0], e[1]));
+            if (pr->two[c]) EF_CUDA(cudaEventElapsedTime(&y, e[1], e[2]));
+            a += x;
+            b += y;
+        }
+    }
+    if (ms_first) *ms_first = a;
+    if (ms_second) *ms_second = b;
+    if (calls) *calls = n;
+    return EF_OK;
 }
 
 int ef_assemble_host(ef_plan* plan, const double* h_nodes, const double* h_coeff, double* h_Kval, double* h_Mval,
@@ -343,6 +505,8 @@ void ef_plan_destroy(ef_plan* plan)
 {
     if (!plan) return;
     cudaDeviceSynchronize();
+    profile_free(plan);
+    plan_queue_free(plan);
     release_work_order(plan);
     free_plan_memory(plan);
     free(plan);

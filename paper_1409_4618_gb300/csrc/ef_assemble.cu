@@ -21,11 +21,9 @@
 // slot through the plan's inverse map; a warp of the sum then reads one
 // contiguous run and its per-item data (list start, CSR positions) coalesced.
 //
-// Pipelined form (ef_assemble with more than one chunk, ef_plan_set_pipeline):
-// the element kernel runs chunk by chunk on the caller's stream; after each
-// chunk an event lets the plan's sum stream add up the nonzeros that chunk
-// completed, while the next chunk computes; the caller's stream waits for the
-// last sum (fork/join by events).
+// The chunking of the work order (the chunk that completes each nonzero) is
+// what the persistent queue of ef_queue.cu interleaves; the kernels here are
+// the plain two-pass form (ef_assemble_two_pass).
 #include "ef_assemble.cuh"
 #include "ef_internal.cuh"
 
@@ -179,24 +177,12 @@ int order_by_count(const uint32_t* seg, uint32_t* list, int64_t n, uint64_t* key
     return EF_OK;
 }
 
-void destroy_pipeline(ef_plan* p)
-{
-    for (int c = 0; c < EF_MAX_CHUNKS + 2; c++)
-        if (p->pc_ev[c]) {
-            cudaEventDestroy(p->pc_ev[c]);
-            p->pc_ev[c] = nullptr;
-        }
-    if (p->pc_aux) cudaStreamDestroy(p->pc_aux);
-    p->pc_aux = nullptr;
-    p->pc_chunks = 0;
-}
-
 // Work order and contribution-list layout for `nchunks` element chunks
 // (1 = plain two-pass): the order of the sums, their list ranges, CSR
 // positions, the element kernel's write positions, and the plan streams.
 int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
 {
-    destroy_pipeline(p);
+    p->pc_chunks = 0;
     free_work_order(p);
     if (p->U == 0) return EF_OK;
     if (nchunks < 1 || nchunks > EF_MAX_CHUNKS) return EF_ERR_ARG;
@@ -252,60 +238,28 @@ int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
     p->pc_chunk = chunk;
     p->pc_woff[0] = 0;
     for (int c = 0; c < nc; c++) p->pc_woff[c + 1] = p->pc_woff[c] + hc[c];
-    if (nc > 1) {
-        int lo, hi;
-        EF_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        EF_CUDA(cudaStreamCreateWithPriority(&p->pc_aux, cudaStreamNonBlocking, hi));
-        for (int c = 0; c <= nc; c++) EF_CUDA(cudaEventCreateWithFlags(&p->pc_ev[c], cudaEventDisableTiming));
-    }
     return EF_OK;
 }
 
 int default_pipeline_chunks(const ef_plan* p)
 {
     if (p->flags & EF_PLAN_NO_PIPELINE) return 1;
-    // enough elements per chunk for several waves of the element kernel
-    int64_t c = p->T / 393216;
+    // chunks of at least 32K elements, at most 16 of them
+    int64_t c = p->T / 32768;
     if (c < 1) c = 1;
-    if (c > 4) c = 4;
+    if (c > EF_MAX_CHUNKS) c = EF_MAX_CHUNKS;
     return (int)c;
 }
 
-void release_work_order(ef_plan* p)
-{
-    destroy_pipeline(p);
-    free_work_order(p);
-}
+void release_work_order(ef_plan* p) { free_work_order(p); }
 
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
                     cudaStream_t s)
 {
     if (p->T == 0) return EF_OK;
     EF_TRY(element_range(p, nodes, coeff, 0, p->T, s));
+    profile_mid(p, s);
     return scatter_range(p, 0, p->U, K, M, s);
-}
-
-int launch_pipelined(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
-                     cudaStream_t s)
-{
-    if (p->T == 0) return EF_OK;
-    const int nc = p->pc_chunks;
-    if (nc <= 1) return launch_two_pass(p, nodes, coeff, K, M, s);
-    // fork: the sum stream starts after the caller's prior work
-    EF_CUDA(cudaEventRecord(p->pc_ev[nc], s));
-    EF_CUDA(cudaStreamWaitEvent(p->pc_aux, p->pc_ev[nc], 0));
-    for (int c = 0; c < nc; c++) {
-        const int64_t e0 = (int64_t)c * p->pc_chunk;
-        const int64_t e1 = e0 + p->pc_chunk < p->T ? e0 + p->pc_chunk : p->T;
-        EF_TRY(element_range(p, nodes, coeff, e0, e1, s));
-        EF_CUDA(cudaEventRecord(p->pc_ev[c], s));
-        EF_CUDA(cudaStreamWaitEvent(p->pc_aux, p->pc_ev[c], 0));
-        EF_TRY(scatter_range(p, (int64_t)p->pc_woff[c], (int64_t)p->pc_woff[c + 1], K, M, p->pc_aux));
-    }
-    // join: the caller's stream waits for the last sum
-    EF_CUDA(cudaEventRecord(p->pc_ev[nc], p->pc_aux));
-    EF_CUDA(cudaStreamWaitEvent(s, p->pc_ev[nc], 0));
-    return EF_OK;
 }
 
 }  // namespace ef

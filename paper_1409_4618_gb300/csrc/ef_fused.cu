@@ -259,6 +259,7 @@ int launch_fused_t(const ef_plan* p, const double* nodes, const double* coeff, d
     k_fused<VAR, BE><<<(unsigned)p->fb_nblocks, BE, smem, s>>>(p->d_elems, nodes, coeff, p->T, p->d_fb_cidx,
                                                                 p->d_fb_slot_off, p->d_fb_sinfo, p->d_fb_posA,
                                                                 p->d_fb_posB, K, M, partK, partM, p->d_status);
+    profile_mid(p, s);
     if (p->n_px > 0)
         k_fixup<<<grid_for(p->n_px), TPB, 0, s>>>(p->d_px_uid, p->n_px, p->d_seg, p->d_pos_up, p->d_pos_lo, partK,
                                                   partM, K, M);

@@ -68,6 +68,11 @@ inline int bits_for(uint64_t max_value)
 }  // namespace ef
 
 #define EF_MAX_CHUNKS 16
+
+namespace ef {
+struct Queue;
+struct Profile;
+}
 #define EF_PLAN_NO_PIPELINE 1   // members of a batch: one chunk, no plan streams
 #define EF_PLAN_NO_ADJOINT 2    // no adjoint incidence / scratch
 
@@ -118,16 +123,19 @@ struct ef_plan {
     double* d_adj_part;      // T * 4 * 3: per (element, vertex) gradient
     double* d_adj_jpart;     // per-CTA partial energies
 
-    // pipelined two-pass: element chunks on the caller's stream, sums on pc_aux
-    int pc_chunks;                       // number of element chunks (<= 1: not pipelined)
+    // chunking of the work order, interleaved by the persistent queue (ef_queue.cu)
+    int pc_chunks;                       // number of element chunks
     int64_t pc_chunk;                    // elements per chunk
     uint32_t pc_woff[EF_MAX_CHUNKS + 1]; // work-list range of the sums each chunk completes
-    cudaStream_t pc_aux;                 // sums
-    cudaEvent_t pc_ev[EF_MAX_CHUNKS + 2];
+    struct ef::Queue* queue;             // the single-launch schedule of ef_assemble
     int use_blocked;                     // ef_assemble runs the element-block kernel (ef_plan_set_block)
+    int use_two_pass;                    // ef_assemble runs the plain two-pass kernels (chosen by ef_plan_tune)
 
     // host staging for ef_assemble_host
     double *d_stage_nodes, *d_stage_coeff, *d_stage_K, *d_stage_M;
+
+    // per-kernel CUDA events of ef_assemble calls (ef_plan_profile)
+    struct ef::Profile* prof;
 };
 
 namespace ef {
@@ -148,10 +156,18 @@ int build_fused_block(ef_plan* p, int BE, cudaStream_t s);
 bool fused_block_supported(int BE);
 int build_adjoint(ef_plan* p, cudaStream_t s);
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);
-int launch_pipelined(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
-                     cudaStream_t s);
-void destroy_pipeline(ef_plan* p);
+int plan_queue_rebuild(ef_plan* p, cudaStream_t s);
+int plan_queue_config(ef_plan* p, const ef_batch_config_t& cfg, cudaStream_t s);
+int queue_max_ctas_per_sm(int variant, int BE);
+void plan_queue_free(ef_plan* p);
+int launch_queue(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);
 int launch_fused(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);
+// Events of ef_plan_profile: recorded before the call's first kernel, between
+// its first and second kernel, and after its last kernel.
+void profile_begin(const ef_plan* p, cudaStream_t s);
+void profile_mid(const ef_plan* p, cudaStream_t s);
+void profile_end(const ef_plan* p, cudaStream_t s);
+void profile_free(ef_plan* p);
 int launch_adjoint(const ef_plan* p, const double* nodes, const double* coeff, const double* u, const double* v,
                    double* J, double* gx, double* gs, cudaStream_t s);
 }  // namespace ef

@@ -55,7 +55,7 @@ class PlanInfo(C.Structure):
 
 class BatchConfig(C.Structure):
     _fields_ = [("elems_per_tile", C.c_int32), ("sum_tile", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("dynamic", C.c_int32), ("largest_first", C.c_int32)]
+                ("dynamic", C.c_int32), ("largest_first", C.c_int32), ("elem_ctas", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +90,8 @@ def load():
             "ef_plan_set_block": ([P, I, P], I),
             "ef_plan_set_pipeline": ([P, I, P], I),
             "ef_plan_tune": ([P, P, P, P, P, I, C.POINTER(C.c_int), P], I),
+            "ef_plan_profile": ([P, I], I),
+            "ef_plan_profile_read": ([P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)], I),
             "ef_plan_topology": ([P, P, P, P, P], I),
             "ef_assemble": ([P, P, P, P, P, P], I),
             "ef_assemble_two_pass": ([P, P, P, P, P, P], I),
@@ -167,6 +169,17 @@ def ef_plan_info(plan) -> dict:
     info = PlanInfo()
     _check(load().ef_plan_info(plan, C.byref(info)))
     return info.as_dict()
+
+
+def ef_plan_profile(plan, max_calls: int):
+    _check(load().ef_plan_profile(plan, int(max_calls)))
+
+
+def ef_plan_profile_read(plan) -> tuple[float, float, int]:
+    """(ms of the first kernel, ms of the second, calls) summed over the recorded ef_assemble calls."""
+    a, b, n = C.c_double(), C.c_double(), C.c_int()
+    _check(load().ef_plan_profile_read(plan, C.byref(a), C.byref(b), C.byref(n)))
+    return a.value, b.value, n.value
 
 
 def ef_plan_set_block(plan, block: int, stream=None):
@@ -277,6 +290,13 @@ class Plan:
     def info(self) -> dict:
         return ef_plan_info(self.handle)
 
+    def profile(self, max_calls: int):
+        """Record per-kernel CUDA events for the next max_calls assemble calls (0 stops)."""
+        ef_plan_profile(self.handle, max_calls)
+
+    def profile_read(self) -> tuple[float, float, int]:
+        return ef_plan_profile_read(self.handle)
+
     def set_block(self, block: int, stream=None):
         ef_plan_set_block(self.handle, block, stream)
 
@@ -284,7 +304,8 @@ class Plan:
         _check(load().ef_plan_set_pipeline(self.handle, int(chunks), _stream_ptr(stream)))
 
     def tune(self, nodes, coeff=None, K=None, M=None, reps: int = 5, stream=None) -> int:
-        """Pick the fastest ef_assemble schedule for this plan; returns chunks (or -block)."""
+        """Pick the fastest ef_assemble schedule for this plan: 0 (two-pass), chunks*100 + elem_ctas*10 + (tile
+        == 256) (persistent queue) or -block (element-block path)."""
         K, M = self._vals(K, M)
         chosen = C.c_int(0)
         _check(load().ef_plan_tune(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),

@@ -79,11 +79,11 @@ def test_batch_every_schedule_and_the_tuner():
     meshes = _meshes(NED1, 9, 1, 12, 8)
     batch, nodes, elems, coeff, K, M, ref = _setup(NED1, meshes)
     for tile in (128, 256):
-        for dyn in (0, 1):
+        for dyn, ec in ((0, 0), (1, 0), (1, 1), (1, 3)):
             for lf in (0, 1):
                 for st in (256, 4096):
                     batch.set_config(elems_per_tile=tile, dynamic=dyn, largest_first=lf, sum_tile=max(st, tile),
-                                     ctas_per_sm=1)
+                                     ctas_per_sm=4 if ec else 1, elem_ctas=ec)
                     for k in K + M:
                         k.fill_(float("nan"))
                     batch.assemble()

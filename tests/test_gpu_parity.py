@@ -5,9 +5,9 @@ bit the oracle's; K and M values within 1e-12 of the entry scale defined in
 tests/_parity.py. Sizes span many 256-element tiles with ragged tails; local
 node order and element order are shuffled so that det B_K takes both signs;
 edge cases: one element, no element, unused nodes, the L-shaped domain. Every
-assembly path (pipelined default, plain two-pass, element-block with 128 or
-256 elements per CTA) is checked, and the default path also inside a CUDA
-graph.
+assembly schedule (the default two-pass kernels, the one-launch persistent
+queue, element-block with 128 or 256 elements per CTA) is checked, and the
+default path also inside a CUDA graph.
 """
 import numpy as np
 import pytest
@@ -59,7 +59,7 @@ CASES = ["c1_rt2d_32", "ned2d_33_shuffled", "rt2d_37_shuffled", "ned3d_8", "ned3
 
 
 @pytest.mark.parametrize("name", CASES)
-@pytest.mark.parametrize("path", ["default", "two_pass", "blocked128", "blocked256"])
+@pytest.mark.parametrize("path", ["default", "chunks4", "blocked128", "blocked256"])
 def test_parity(ora, name, path):
     kind, dim, nodes, elems, coeff = _case(name)
     o = ora.assemble(kind, dim, nodes, elems, coeff)
@@ -88,9 +88,9 @@ def test_empty_mesh(kind, dim):
 
 @pytest.mark.parametrize("kind", [NED1, RT0])
 def test_paths_agree_bitwise_and_runs_repeat(ora, kind):
-    """Pipelined (several element chunks at 131,712 tets), plain two-pass and
-    element-block paths form the same sums in the same order: identical bits,
-    run after run; and the pipelined result passes parity."""
+    """The persistent queue (several element chunks at 131,712 tets), the plain
+    two-pass and the element-block paths form the same sums in the same order:
+    identical bits, run after run; and the queue's result passes parity."""
     nodes, elems = mg.kuhn_cube(28, 0.2, 12)
     coeff = mg.log_uniform_coeff(12, elems.shape[0])
     a = run_gpu(kind, 3, nodes, elems, coeff, path="chunks3")
@@ -148,17 +148,47 @@ def test_tuner_keeps_results_and_picks_a_schedule():
 
     from paper_1409_4618_gb300 import edgefem as ef
 
-    nodes, elems = mg.kuhn_cube(36, 0.2, 14)           # 279,936 tets: pipelines up to 4 chunks are tried
+    nodes, elems = mg.kuhn_cube(36, 0.2, 14)           # 279,936 tets: 4, 8 and 16 chunks are tried
     coeff = mg.log_uniform_coeff(14, elems.shape[0])
     tn, tc = torch.from_numpy(nodes).cuda(), torch.from_numpy(coeff).cuda()
     plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).cuda())
     K0, M0 = plan.assemble_two_pass(tn, tc)
     chosen = plan.tune(tn, tc, reps=2)
-    assert chosen in (1, 2, 3, 4, -128, -256)
+    assert chosen in (0, -128, -256) or (chosen // 100 in (4, 8, 16) and (chosen // 10) % 10 in (0, 1, 2))
     K, M = plan.assemble(tn, tc)
     torch.cuda.synchronize()
     assert torch.equal(K.view(torch.int64), K0.view(torch.int64))
     assert torch.equal(M.view(torch.int64), M0.view(torch.int64))
+    plan.close()
+
+
+def test_kernel_profile_events():
+    """ef_plan_profile records the kernels of exactly the requested number of
+    calls; the two-pass schedule reports both kernels, the one-launch queue
+    all its time as the first kernel."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(20, 0.2, 15)
+    tn = torch.from_numpy(nodes).cuda()
+    plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).cuda())
+    K = torch.empty(plan.nnz, dtype=torch.float64, device="cuda")
+    M = torch.empty_like(K)
+    assert plan.info()["assemble_launches"] == 2
+    plan.profile(3)
+    for _ in range(5):
+        plan.assemble(tn, None, K, M)
+    first, second, calls = plan.profile_read()
+    assert calls == 3 and first > 0 and second > 0
+    plan.set_pipeline(4)
+    plan.profile(2)
+    for _ in range(2):
+        plan.assemble(tn, None, K, M)
+    first, second, calls = plan.profile_read()
+    assert calls == 2 and first > 0 and second == 0
+    plan.profile(0)
+    assert plan.profile_read() == (0.0, 0.0, 0)
     plan.close()
 
 
@@ -196,8 +226,9 @@ def test_errors_are_reported():
 
 
 def test_cuda_graph_capture_replays_bitwise():
-    """ef_assemble (the pipelined fork/join across two streams) captured in a
-    CUDA graph and replayed gives the same bits as a direct call."""
+    """ef_assemble (one persistent launch with self-resetting queue counters)
+    captured in a CUDA graph and replayed gives the same bits as a direct
+    call, also after the coordinates change in place."""
     import torch
 
     from paper_1409_4618_gb300 import edgefem as ef
