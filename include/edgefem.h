@@ -180,9 +180,13 @@ int ef_assemble_two_pass(const ef_plan* plan, const double* d_nodes, const doubl
  * End-to-end form for host data: copies h_nodes (n_nodes x dim) and h_coeff
  * (n_elems, or NULL) to plan-owned device staging buffers, assembles, and
  * copies K and M values back into h_Kval / h_Mval (nnz doubles each). Host
- * buffers should be pinned for asynchronous copies. Synchronises `stream`
+ * buffers should be pinned for asynchronous copies. When the plan's work
+ * order has several element chunks (the default from 65,536 elements on),
+ * the two-pass kernels run chunk by chunk and the CSR rows that a chunk
+ * leaves final are copied back on a plan-owned stream while the next chunks
+ * compute; values are the same bits as ef_assemble's. Synchronises `stream`
  * before returning and reports degenerate elements (EF_ERR_DEGENERATE).
- * The first call allocates the staging buffers.
+ * The first call allocates the staging buffers, the copy stream and events.
  */
 int ef_assemble_host(ef_plan* plan, const double* h_nodes, const double* h_coeff, double* h_Kval, double* h_Mval,
                      void* stream);

@@ -22,6 +22,9 @@ void free_plan_memory(ef_plan* p)
                     p->d_node_off,  p->d_node_inc,   p->d_adj_part,  p->d_adj_jpart};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    for (cudaEvent_t e : p->copy_ev)
+        if (e) cudaEventDestroy(e);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
 }
 
 int plan_args(int kind, int dim, int64_t n_nodes, int64_t n_elems, const void* d_elems)
@@ -280,7 +283,7 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
     {
         Cand k{};
         k.two_pass = 1;
-        k.chunks = 1;
+        k.chunks = default_pipeline_chunks(plan);
         cands.push_back(k);
     }
     const int chunk_opts[] = {4, 8, 16};
@@ -313,7 +316,10 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
         if (c.block > 0)
             st = ef_plan_set_block(plan, c.block, stream);
         else if (c.two_pass) {
-            if (plan->pc_chunks != 1) st = ef_plan_set_pipeline(plan, 1, stream);
+            // the two-pass kernels do not depend on the chunking; keep the
+            // default one, which ef_assemble_host overlaps with its copies
+            if (plan->pc_chunks != c.chunks) st = ef_plan_set_pipeline(plan, c.chunks, stream);
+            plan->use_blocked = 0;
             plan->use_two_pass = 1;
         } else {
             if (plan->pc_chunks != c.chunks) st = ef_plan_set_pipeline(plan, c.chunks, stream);
@@ -345,7 +351,7 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
         st = ef_plan_set_block(plan, c.block, stream);
         if (chosen) *chosen = -c.block;
     } else if (c.two_pass) {
-        st = ef_plan_set_pipeline(plan, 1, stream);
+        st = ef_plan_set_pipeline(plan, c.chunks, stream);
         plan->use_two_pass = 1;
         if (chosen) *chosen = 0;
     } else {
@@ -471,12 +477,39 @@ int ef_assemble_host(ef_plan* plan, const double* h_nodes, const double* h_coeff
         EF_CUDA(cudaMemcpyAsync(plan->d_stage_nodes, h_nodes, (size_t)plan->V * plan->dim * 8, cudaMemcpyHostToDevice, s));
     if (h_coeff && plan->T > 0)
         EF_CUDA(cudaMemcpyAsync(plan->d_stage_coeff, h_coeff, (size_t)plan->T * 8, cudaMemcpyHostToDevice, s));
-    EF_TRY(ef_assemble(plan, plan->d_stage_nodes, h_coeff ? plan->d_stage_coeff : nullptr, plan->d_stage_K,
-                       plan->d_stage_M, stream));
-    if (plan->nnz > 0) {
-        EF_CUDA(cudaMemcpyAsync(h_Kval, plan->d_stage_K, (size_t)plan->nnz * 8, cudaMemcpyDeviceToHost, s));
-        EF_CUDA(cudaMemcpyAsync(h_Mval, plan->d_stage_M, (size_t)plan->nnz * 8, cudaMemcpyDeviceToHost, s));
+    const double* dn = plan->d_stage_nodes;
+    const double* dc = h_coeff ? plan->d_stage_coeff : nullptr;
+    double *dK = plan->d_stage_K, *dM = plan->d_stage_M;
+    const bool chunked = plan->T > 0 && plan->pc_chunks > 1 && !(plan->use_blocked && plan->fb_nblocks > 0);
+    if (!chunked) {
+        EF_TRY(ef_assemble(plan, dn, dc, dK, dM, stream));
+        if (plan->nnz > 0) {
+            EF_CUDA(cudaMemcpyAsync(h_Kval, dK, (size_t)plan->nnz * 8, cudaMemcpyDeviceToHost, s));
+            EF_CUDA(cudaMemcpyAsync(h_Mval, dM, (size_t)plan->nnz * 8, cudaMemcpyDeviceToHost, s));
+        }
+        return ef_plan_check(plan, stream);
     }
+    // Chunked: element chunk c and the sums it completes run on `stream`;
+    // the CSR entries that are final after chunk c go back to the host on
+    // the plan's copy stream while the next chunks compute.
+    if (!plan->copy_stream) EF_CUDA(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : plan->copy_ev)
+        if (!e) EF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaStream_t cs = plan->copy_stream;
+    int64_t sent = 0;
+    for (int c = 0; c < plan->pc_chunks; c++) {
+        EF_TRY(launch_two_pass_chunk(plan, c, dn, dc, dK, dM, s));
+        const int64_t done = plan->pc_csr_done[c + 1];
+        if (done > sent) {
+            EF_CUDA(cudaEventRecord(plan->copy_ev[c], s));
+            EF_CUDA(cudaStreamWaitEvent(cs, plan->copy_ev[c], 0));
+            EF_CUDA(cudaMemcpyAsync(h_Kval + sent, dK + sent, (size_t)(done - sent) * 8, cudaMemcpyDeviceToHost, cs));
+            EF_CUDA(cudaMemcpyAsync(h_Mval + sent, dM + sent, (size_t)(done - sent) * 8, cudaMemcpyDeviceToHost, cs));
+            sent = done;
+        }
+    }
+    EF_CUDA(cudaEventRecord(plan->copy_ev[EF_MAX_CHUNKS], cs));
+    EF_CUDA(cudaStreamWaitEvent(s, plan->copy_ev[EF_MAX_CHUNKS], 0));
     return ef_plan_check(plan, stream);
 }
 

@@ -118,6 +118,44 @@ __global__ void __launch_bounds__(TPB) k_scatter(int64_t w0, int64_t w1, const u
     }
 }
 
+// Latest completing chunk of every CSR row: row r is final once every upper
+// nonzero in row r or column r is summed.
+__global__ void k_row_last_chunk(const uint32_t* seg, const uint32_t* perm, const uint32_t* pos_up,
+                                 const uint32_t* pos_lo, const int32_t* colidx, int64_t U, int64_t T, int64_t chunk,
+                                 uint32_t* row_last)
+{
+    const int64_t u = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (u >= U) return;
+    const uint32_t rc = (uint32_t)((perm[seg[u + 1] - 1] % T) / chunk);
+    const uint32_t j = (uint32_t)colidx[pos_up[u]];
+    if (rc) atomicMax(row_last + j, rc);
+    const uint32_t pl = pos_lo[u];
+    if (pl != 0xffffffffu && rc) atomicMax(row_last + colidx[pl], rc);
+}
+
+// first_row[c] = smallest row whose last chunk is > c (rows before it are
+// final after chunks 0..c); a CTA reduces in shared memory first.
+__global__ void k_first_open_row(const uint32_t* row_last, int64_t N, int nc, uint32_t* first_row)
+{
+    __shared__ uint32_t s_min[EF_MAX_CHUNKS];
+    if (threadIdx.x < EF_MAX_CHUNKS) s_min[threadIdx.x] = 0xffffffffu;
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (r < N)
+        for (uint32_t c = 0; c < row_last[r]; c++) atomicMin(&s_min[c], (uint32_t)r);
+    __syncthreads();
+    if (threadIdx.x < nc && s_min[threadIdx.x] != 0xffffffffu) atomicMin(first_row + threadIdx.x, s_min[threadIdx.x]);
+}
+
+__global__ void k_rows_to_positions(const uint32_t* first_row, const int64_t* rowptr, int64_t N, int nc,
+                                    int64_t* pos)
+{
+    const int c = threadIdx.x;
+    if (c >= nc) return;
+    const uint32_t r = first_row[c];
+    pos[c] = rowptr[r < N ? r : N];
+}
+
 __global__ void k_count_keys(const uint32_t* seg, const uint32_t* list, int64_t n, uint64_t* keys, uint32_t* vals)
 {
     const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -215,9 +253,26 @@ int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
                                         p->d_wpos_lo);
         st = exclusive_scan_u32(wcnt, p->d_wseg, U, true, tmp, s);
     }
+    int64_t hpos[EF_MAX_CHUNKS] = {0};
     if (st == EF_OK) {
         k_work_inv<<<gu, TPB, 0, s>>>(order, U, p->d_seg, p->d_perm, p->d_wseg, p->d_inv);
         cudaMemcpyAsync(hc, cnt, EF_MAX_CHUNKS * 4, cudaMemcpyDeviceToHost, s);
+        // CSR prefix that is final after each chunk (the scratch `order` and
+        // `keys` are free again): rows' last chunks, first open row, position
+        uint32_t* row_last = (uint32_t*)keys;                       // N entries (N <= 2 U)
+        uint32_t* first_row = cnt;
+        int64_t* pos = (int64_t*)order;
+        if ((int64_t)p->N * 4 > U * 8) {
+            st = EF_ERR_ARG;   // cannot happen: every row holds a diagonal upper nonzero
+        } else {
+            cudaMemsetAsync(row_last, 0, (size_t)p->N * 4, s);
+            k_row_last_chunk<<<gu, TPB, 0, s>>>(p->d_seg, p->d_perm, p->d_pos_up, p->d_pos_lo, p->d_colidx, U, T,
+                                                 chunk, row_last);
+            cudaMemsetAsync(first_row, 0xff, EF_MAX_CHUNKS * 4, s);
+            k_first_open_row<<<(unsigned)((p->N + TPB - 1) / TPB), TPB, 0, s>>>(row_last, p->N, nc, first_row);
+            k_rows_to_positions<<<1, 32, 0, s>>>(first_row, p->d_rowptr, p->N, nc, pos);
+            cudaMemcpyAsync(hpos, pos, sizeof(int64_t) * nc, cudaMemcpyDeviceToHost, s);
+        }
         cudaError_t e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -238,6 +293,9 @@ int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
     p->pc_chunk = chunk;
     p->pc_woff[0] = 0;
     for (int c = 0; c < nc; c++) p->pc_woff[c + 1] = p->pc_woff[c] + hc[c];
+    p->pc_csr_done[0] = 0;
+    for (int c = 0; c < nc; c++) p->pc_csr_done[c + 1] = hpos[c] > p->pc_csr_done[c] ? hpos[c] : p->pc_csr_done[c];
+    p->pc_csr_done[nc] = p->nnz;
     return EF_OK;
 }
 
@@ -252,6 +310,16 @@ int default_pipeline_chunks(const ef_plan* p)
 }
 
 void release_work_order(ef_plan* p) { free_work_order(p); }
+
+int launch_two_pass_chunk(const ef_plan* p, int c, const double* nodes, const double* coeff, double* K, double* M,
+                          cudaStream_t s)
+{
+    if (c < 0 || c >= p->pc_chunks) return EF_ERR_ARG;
+    const int64_t e0 = (int64_t)c * p->pc_chunk;
+    const int64_t e1 = e0 + p->pc_chunk < p->T ? e0 + p->pc_chunk : p->T;
+    EF_TRY(element_range(p, nodes, coeff, e0, e1, s));
+    return scatter_range(p, p->pc_woff[c], p->pc_woff[c + 1], K, M, s);
+}
 
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
                     cudaStream_t s)

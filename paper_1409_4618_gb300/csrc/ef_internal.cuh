@@ -127,12 +127,15 @@ struct ef_plan {
     int pc_chunks;                       // number of element chunks
     int64_t pc_chunk;                    // elements per chunk
     uint32_t pc_woff[EF_MAX_CHUNKS + 1]; // work-list range of the sums each chunk completes
+    int64_t pc_csr_done[EF_MAX_CHUNKS + 1]; // CSR entries [0, pc_csr_done[c+1]) are final after chunks 0..c
     struct ef::Queue* queue;             // the single-launch schedule of ef_assemble
     int use_blocked;                     // ef_assemble runs the element-block kernel (ef_plan_set_block)
     int use_two_pass;                    // ef_assemble runs the plain two-pass kernels (chosen by ef_plan_tune)
 
-    // host staging for ef_assemble_host
+    // host staging for ef_assemble_host, and its copy stream and chunk events
     double *d_stage_nodes, *d_stage_coeff, *d_stage_K, *d_stage_M;
+    cudaStream_t copy_stream;
+    cudaEvent_t copy_ev[EF_MAX_CHUNKS + 1];
 
     // per-kernel CUDA events of ef_assemble calls (ef_plan_profile)
     struct ef::Profile* prof;
@@ -156,6 +159,9 @@ int build_fused_block(ef_plan* p, int BE, cudaStream_t s);
 bool fused_block_supported(int BE);
 int build_adjoint(ef_plan* p, cudaStream_t s);
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);
+// Element chunk c of the work order and the sums it completes.
+int launch_two_pass_chunk(const ef_plan* p, int c, const double* nodes, const double* coeff, double* K, double* M,
+                          cudaStream_t s);
 int plan_queue_rebuild(ef_plan* p, cudaStream_t s);
 int plan_queue_config(ef_plan* p, const ef_batch_config_t& cfg, cudaStream_t s);
 int queue_max_ctas_per_sm(int variant, int BE);

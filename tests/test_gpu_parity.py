@@ -143,6 +143,32 @@ def test_one_shot_and_host_path_match_plan(ora):
     assert np.abs(rt["K"].cpu().numpy() - o["K"]).max() <= 1e-12 * np.abs(o["K"]).max()
 
 
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_host_path_chunked_copies_only_final_rows(shuffle):
+    """ef_assemble_host on a plan with several element chunks copies each CSR
+    range back only once every sum in it is done: a first call with other
+    coefficients leaves different values in the staging buffers, so a range
+    copied too early would differ from the device result. With the elements
+    shuffled, rows become final only near the end; the result is the same."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(28, 0.2, 16)                 # 131,712 tets: 4 element chunks
+    if shuffle:
+        elems = elems[np.argsort(mg.uniform(16, 11, np.arange(elems.shape[0])))]
+    coeff = mg.log_uniform_coeff(16, elems.shape[0])
+    plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(np.ascontiguousarray(elems)).cuda())
+    assert plan.info()["pipeline_chunks"] == 4
+    K0, M0 = plan.assemble(torch.from_numpy(nodes).cuda(), torch.from_numpy(coeff).cuda())
+    hn = torch.from_numpy(nodes).pin_memory()
+    plan.assemble_host(hn, torch.from_numpy(3.0 * coeff).pin_memory())
+    K, M = plan.assemble_host(hn, torch.from_numpy(coeff).pin_memory())
+    assert torch.equal(K.view(torch.int64), K0.cpu().view(torch.int64))
+    assert torch.equal(M.view(torch.int64), M0.cpu().view(torch.int64))
+    plan.close()
+
+
 def test_tuner_keeps_results_and_picks_a_schedule():
     import torch
 
