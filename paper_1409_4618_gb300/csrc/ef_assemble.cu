@@ -36,7 +36,7 @@ constexpr int TPB = 256;
 // list: inv[q * T + e] = position of (element e, pair q). K values occupy
 // list[0, np T), M values list[np T, 2 np T).
 template <int VAR>
-__global__ void __launch_bounds__(TPB, 4) k_element_local(const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(TPB, 3) k_element_local(const int32_t* __restrict__ elems,
                                                        const double* __restrict__ nodes,
                                                        const double* __restrict__ coeff,
                                                        const uint32_t* __restrict__ inv, int64_t e0, int64_t e1,

@@ -125,11 +125,23 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     const double k23 = h23 - h13, k24 = h12 - h11, k25 = h22 - h12;
     const double k00 = k03 - k05, k11 = k14 - k13, k22 = k25 - k24;
     const double k01 = k04 - k03, k02 = k05 - k04, k12 = k15 - k14;
-    // M: Whitney-form combinations of g = sigma/(120|det|) adj(H), node 0 row from sum-zero
+    // M: Whitney-form combinations of g = sigma/(120|det|) adj(H) (the
+    // scaled Gram matrix of grad lambda_1..3). With p_ab = -G_ab for the six
+    // node pairs (the row of node 0 from the zero row sums), S_a = G_aa, and
+    // o = p_e + p_e' over the three pairs of opposite edges (e, e'), the
+    // Whitney mass entries |K|/20 int (lambda_a grad lambda_b - ...) . (...)
+    // reduce to: diagonal 2 (S_a + S_b + p_ab) = 2 (o_i + o_j + 3 p_e) (o_i,
+    // o_j the two other pairs); edges sharing node s with other ends u, v:
+    // +-(2 S_s - (p_uv + o(uv))); disjoint edges (a,b), (c,d): p_ad + p_bc -
+    // p_ac - p_bd, a difference of two o's. 41 operations after the scaling.
     const double cM = sr * (1.0 / 120.0);
     const double g11 = cM * A11, g22 = cM * A22, g33 = cM * A33, g12 = cM * A12, g13 = cM * A13, g23 = cM * A23;
-    const double g01 = -(g11 + g12 + g13), g02 = -(g12 + g22 + g23), g03 = -(g13 + g23 + g33);
-    const double g00 = -(g01 + g02 + g03);
+    const double p01 = g11 + g12 + g13, p02 = g12 + g22 + g23, p03 = g13 + g23 + g33;   // p12 = -g12, ...
+    const double S0 = p01 + p02 + p03;
+    const double oA = p01 - g23, oB = p02 - g13, oC = p03 - g12;   // {01,23}, {02,13}, {03,12}
+    const double QA = oB + oC, QB = oA + oC, QC = oA + oB;
+    const double r01 = oA + p01, r02 = oB + p02, r03 = oC + p03;
+    const double r12 = oC - g12, r13 = oB - g13, r23 = oA - g23;
 
     // order: (0,0)..(0,5), (1,1)..(1,5), (2,2)..(2,5), (3,3)..(3,5), (4,4),(4,5), (5,5)
     Kq[0] = k00; Kq[1] = k01; Kq[2] = k02; Kq[3] = k03; Kq[4] = k04; Kq[5] = k05;
@@ -139,30 +151,28 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     Kq[18] = h11; Kq[19] = h12;
     Kq[20] = h22;
 
-    // shared differences: a_i = g00 - g0i, d12 = g11 - g12, d23 = g22 - g23, d31 = g33 - g13
-    const double a1 = g00 - g01, a2 = g00 - g02, a3 = g00 - g03;
-    const double d12 = g11 - g12, d23 = g22 - g23, d31 = g33 - g13;
-    Mq[0] = twice(a1 + g11);                          // 2 (g00 + g11 - g01)
-    Mq[1] = fma(2.0, g12, a1 - g02);
-    Mq[2] = fma(2.0, g13, a1 - g03);
-    Mq[3] = fma(-2.0, g02, g01 - d12);
-    Mq[4] = (g13 - g12) - (g03 - g02);
-    Mq[5] = fma(2.0, g03, (g11 - g13) - g01);
-    Mq[6] = twice(a2 + g22);
-    Mq[7] = fma(2.0, g23, a2 - g03);
-    Mq[8] = fma(2.0, g01, (g22 - g12) - g02);
-    Mq[9] = fma(-2.0, g03, g02 - d23);
-    Mq[10] = (g12 - g23) - (g01 - g03);
-    Mq[11] = twice(a3 + g33);
-    Mq[12] = (g23 - g13) - (g02 - g01);
-    Mq[13] = fma(2.0, g02, (g33 - g23) - g03);
-    Mq[14] = fma(-2.0, g01, g03 - d31);
-    Mq[15] = twice(g22 + d12);                        // 2 (g11 + g22 - g12)
-    Mq[16] = fma(-2.0, g13, g12 - d23);
-    Mq[17] = fma(-2.0, g23, g13 - d12);
-    Mq[18] = twice(g33 + d23);
-    Mq[19] = fma(-2.0, g12, g23 - d31);
-    Mq[20] = twice(g11 + d31);
+    // local edges 0..5 = (0,1), (0,2), (0,3), (1,2), (2,3), (3,1)
+    Mq[0] = twice(fma(3.0, p01, QA));
+    Mq[1] = fma(2.0, S0, -r12);
+    Mq[2] = fma(2.0, S0, -r13);
+    Mq[3] = fma(-2.0, g11, r02);
+    Mq[4] = oC - oB;
+    Mq[5] = fma(2.0, g11, -r03);
+    Mq[6] = twice(fma(3.0, p02, QB));
+    Mq[7] = fma(2.0, S0, -r23);
+    Mq[8] = fma(2.0, g22, -r01);
+    Mq[9] = fma(-2.0, g22, r03);
+    Mq[10] = oA - oC;
+    Mq[11] = twice(fma(3.0, p03, QC));
+    Mq[12] = oB - oA;
+    Mq[13] = fma(2.0, g33, -r02);
+    Mq[14] = fma(-2.0, g33, r01);
+    Mq[15] = twice(fma(-3.0, g12, QC));
+    Mq[16] = fma(-2.0, g22, r13);
+    Mq[17] = fma(-2.0, g11, r23);
+    Mq[18] = twice(fma(-3.0, g23, QA));
+    Mq[19] = fma(-2.0, g33, r12);
+    Mq[20] = twice(fma(-3.0, g13, QB));
 
     // signs s_k s_l on the off-diagonal pairs
     int q = 0;
