@@ -49,8 +49,8 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per element of the Nedelec-3D element kernel of
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
 # on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
-# to the elements. None until counters are taken on the current kernel.
-ELEMENT_KERNEL_DRAM_BYTES_PER_TET = None
+# to the elements.
+ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (121.135872e6 + 206.874112e6) / 663552
 
 
 def _peaks():

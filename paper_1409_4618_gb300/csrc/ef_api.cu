@@ -300,7 +300,6 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
                     k.q.largest_first = 0;
                     k.q.elem_ctas = ec;
                     k.q.ctas_per_sm = queue_max_ctas_per_sm(plan->variant, be);
-                    if (ec > 0) k.q.ctas_per_sm = (k.q.ctas_per_sm / 4) * 4;   // whole groups of four
                     if (k.q.ctas_per_sm >= 1) cands.push_back(k);
                 }
     }

@@ -163,7 +163,7 @@ int ef_batch_tune(ef_batch* b, int reps, ef_batch_config_t* best_out, void* stre
                         c.dynamic = dyn;
                         c.largest_first = lf;
                         c.elem_ctas = ec;
-                        c.ctas_per_sm = ec ? (maxc / 4) * 4 : maxc;
+                        c.ctas_per_sm = maxc;
                         if (c.ctas_per_sm < 1) continue;
                         b->queue.cfg = c;
                         if ((st = queue_build(&b->queue, b->plans, s)) != EF_OK) break;

@@ -36,6 +36,10 @@ namespace {
 
 constexpr unsigned kPollLimit = 20000000u;   // ~2-3 s of polling with back-off
 
+// CTAs per SM the kernel is compiled for: 80 registers per thread, enough for
+// the 3D Nedelec element matrices without spills.
+constexpr int queue_min_blocks(int BE) { return BE == 128 ? 6 : 3; }
+
 __device__ __forceinline__ int find_segment(const QueueSegment* __restrict__ seg, int nseg, int64_t k)
 {
     int lo = 0, hi = nseg - 1;   // last segment with tile_off <= k
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
 template <int VAR, int BE>
 int launch_t(const Queue* q, const QueueArgs& a, cudaStream_t s)
 {
-    constexpr int MINB = BE == 128 ? 8 : 4;   // 64 registers per thread
+    constexpr int MINB = queue_min_blocks(BE);
     const int grid = q->cfg.ctas_per_sm * q->sms;
     k_queue<VAR, BE, MINB><<<grid, BE, 0, s>>>(q->d_mesh, q->d_seg, q->nseg, q->d_need, q->ntiles, q->n_elem_tiles,
                                                q->cfg.sum_tile, q->cfg.dynamic, q->cfg.elem_ctas, q->d_ctrl,
@@ -189,8 +193,10 @@ template <int VAR>
 int occupancy_t(int BE)
 {
     int nb = 0;
-    cudaError_t e = BE == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_queue<VAR, 128, 8>, 128, 0)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_queue<VAR, 256, 4>, 256, 0);
+    cudaError_t e = BE == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &nb, k_queue<VAR, 128, queue_min_blocks(128)>, 128, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &nb, k_queue<VAR, 256, queue_min_blocks(256)>, 256, 0);
     return e == cudaSuccess ? nb : 0;
 }
 

@@ -83,7 +83,7 @@ def test_batch_every_schedule_and_the_tuner():
             for lf in (0, 1):
                 for st in (256, 4096):
                     batch.set_config(elems_per_tile=tile, dynamic=dyn, largest_first=lf, sum_tile=max(st, tile),
-                                     ctas_per_sm=4 if ec else 1, elem_ctas=ec)
+                                     ctas_per_sm=2 if ec else 1, elem_ctas=ec)
                     for k in K + M:
                         k.fill_(float("nan"))
                     batch.assemble()
