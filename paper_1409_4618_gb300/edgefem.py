@@ -5,8 +5,9 @@ memory and the current stream. There is no CPU path: if the library is not
 built or no CUDA device is present, the calls raise.
 
 Names follow the C ABI: ``ef_plan_create``, ``ef_assemble``, ...; ``Plan``
-bundles a plan handle with its sizes, and ``rt0_assemble`` / ``ned_assemble``
-are the one-shot calls.
+bundles a plan handle with its sizes, ``rt0_assemble`` / ``ned_assemble``
+are the one-shot calls, and ``energy`` wraps ``ef_adjoint`` as a
+differentiable function of the node coordinates and coefficients.
 """
 from __future__ import annotations
 
@@ -385,6 +386,31 @@ def _ptr_array(tensors, dtype, name, allow_none=False):
         else:
             out[i] = _dev(t, dtype, f"{name}[{i}]")
     return out
+
+
+class _Energy(torch.autograd.Function):
+    """J = u^T K u + v^T M v as a function of (nodes, coeff); the gradient is
+    the one ef_adjoint computes together with J."""
+
+    @staticmethod
+    def forward(ctx, nodes, coeff, u, v, plan):
+        J, gx, gs = plan.adjoint(nodes, coeff, u, v)
+        ctx.save_for_backward(gx, gs)
+        ctx.has_coeff = coeff is not None
+        return J.reshape(())
+
+    @staticmethod
+    def backward(ctx, gJ):
+        gx, gs = ctx.saved_tensors
+        return gJ * gx, (gJ * gs if ctx.has_coeff else None), None, None, None
+
+
+def energy(plan: "Plan", nodes: torch.Tensor, coeff, u: torch.Tensor, v: torch.Tensor) -> torch.Tensor:
+    """Differentiable J(nodes, coeff) = u^T K u + v^T M v of a 3D Nedelec plan
+    (u, v fixed DOF vectors; no gradient flows to them)."""
+    if u.requires_grad or v.requires_grad:
+        raise ValueError("energy: u and v are constants (the library gives dJ/dnodes and dJ/dcoeff only)")
+    return _Energy.apply(nodes, coeff, u, v, plan)
 
 
 class Batch:

@@ -112,3 +112,28 @@ def test_adjoint_bitwise_repeatable():
     assert a[0] == b[0]
     assert np.array_equal(a[1].view(np.uint64), b[1].view(np.uint64))
     assert np.array_equal(a[2].view(np.uint64), b[2].view(np.uint64))
+
+
+def test_energy_autograd_wrapper():
+    """edgefem.energy is J(nodes, coeff) with the library's gradient: the value
+    and (scaled) gradients through torch.autograd equal ef_adjoint's."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems, coeff = _setup(5, 21)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    plan = ef.Plan(NED1, 3, nodes.shape[0], t(elems.astype(np.int32)))
+    u = t(mg.normal(21, mg.STREAM_U, plan.n_dofs))
+    v = t(mg.normal(21, mg.STREAM_V, plan.n_dofs))
+    J0, gx0, gs0 = plan.adjoint(t(nodes), t(coeff), u, v)
+    x = t(nodes).requires_grad_(True)
+    s = t(coeff).requires_grad_(True)
+    J = ef.energy(plan, x, s, u, v)
+    assert J.shape == () and float(J) == float(J0[0])
+    (3.0 * J).backward()
+    assert torch.equal(x.grad, 3.0 * gx0)
+    assert torch.equal(s.grad, 3.0 * gs0)
+    with pytest.raises(ValueError):
+        ef.energy(plan, x, s, u.clone().requires_grad_(True), v)
+    plan.close()
