@@ -19,7 +19,8 @@
 // dJ/dsigma_K = J_K / sigma. Geometry is recomputed here, not stored by the
 // forward pass. The per-(element, vertex) gradients go to plan scratch and are
 // summed per node in ascending element order; J is summed per CTA in a fixed
-// tree and the CTA sums in index order. No floating-point atomics.
+// tree and the CTA sums in a fixed strided order and tree. No floating-point
+// atomics.
 #include "ef_assemble.cuh"
 #include "ef_internal.cuh"
 
@@ -28,7 +29,7 @@ namespace {
 
 constexpr int ADJ_TPB = 256;
 
-__global__ void __launch_bounds__(ADJ_TPB) k_adjoint_ned3(const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(ADJ_TPB, 3) k_adjoint_ned3(const int32_t* __restrict__ elems,
                                                           const double* __restrict__ nodes,
                                                           const double* __restrict__ coeff,
                                                           const int32_t* __restrict__ e2d,
@@ -86,12 +87,10 @@ __global__ void __launch_bounds__(ADJ_TPB) k_adjoint_ned3(const int32_t* __restr
         const double r = 1.0 / adet;
         const double r3 = r * r * r;
 
-        // K part
+        // K part: aHa = a^T H a over the symmetric H
         const double av[3] = {ut[1] - ut[2] + ut[4], ut[2] - ut[0] + ut[5], ut[0] - ut[1] + ut[3]};
-        double Ha[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) Ha[i] = fma(H[i][2], av[2], fma(H[i][1], av[1], H[i][0] * av[0]));
-        const double aHa = fma(av[2], Ha[2], fma(av[1], Ha[1], av[0] * Ha[0]));
+        const double aHa = fma(av[0], fma(H[0][0], av[0], twice(fma(H[0][1], av[1], H[0][2] * av[2]))),
+                               fma(av[1], fma(H[1][1], av[1], twice(H[1][2] * av[2])), av[2] * (H[2][2] * av[2])));
 
         // M part: C antisymmetric over the 4 nodes, edges (0,1),(0,2),(0,3),(1,2),(2,3),(3,1)
         const double c0 = -(vt[0] + vt[1] + vt[2]);
@@ -115,43 +114,44 @@ __global__ void __launch_bounds__(ADJ_TPB) k_adjoint_ned3(const int32_t* __restr
                 P[i][j] = s;
                 P[j][i] = s;
             }
-        double PA = 0.0;
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) PA = fma(P[i][j], A[i][j], PA);
+        // <P, A> over the symmetric pair
+        const double PA = fma(P[0][0], A[0][0], fma(P[1][1], A[1][1], fma(P[2][2], A[2][2],
+                              twice(fma(P[0][1], A[0][1], fma(P[0][2], A[0][2], P[1][2] * A[1][2]))))));
 
         const double J1 = (2.0 / 3.0) * r * aHa + (r / 120.0) * PA;
         if (gcoeff) gcoeff[e] = J1;
         Jloc = sigma * J1;
 
-        // Gamma = (2/3)(r a a^T - r^3/2 aHa A) + r^3/120 (PA/2 A - A P A)
+        // 2 sigma Gamma, Gamma = (2/3)(r a a^T - r^3/2 aHa A) + r^3/120 (PA/2 A - A P A),
+        // symmetric: six entries; A P A from the full A P and the upper half of (A P) A
         double AP[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++) AP[i][j] = fma(A[i][2], P[2][j], fma(A[i][1], P[1][j], A[i][0] * P[0][j]));
-        const double kA = -(1.0 / 3.0) * r3 * aHa + (r3 / 240.0) * PA;
-        const double kaa = (2.0 / 3.0) * r;
-        const double kAPA = -(r3 / 120.0);
+        const double s2 = 2.0 * sigma;
+        const double kA = s2 * (-(1.0 / 3.0) * r3 * aHa + (r3 / 240.0) * PA);
+        const double kAPA = s2 * -(r3 / 120.0);
+        const double kaa = s2 * (2.0 / 3.0) * r;
+        const double ka[3] = {kaa * av[0], kaa * av[1], kaa * av[2]};
         double Gm[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) {
+            for (int j = i; j < 3; j++) {
                 const double apa = fma(AP[i][2], A[2][j], fma(AP[i][1], A[1][j], AP[i][0] * A[0][j]));
-                Gm[i][j] = fma(kAPA, apa, fma(kA, A[i][j], kaa * av[i] * av[j]));
+                Gm[i][j] = fma(kAPA, apa, fma(kA, A[i][j], ka[i] * av[j]));
+                Gm[j][i] = Gm[i][j];
             }
-        // dJ/de_i = 2 sigma (B Gamma)[:, i]
-        const double s2 = 2.0 * sigma;
+        // dJ/de_i = 2 sigma (B Gamma)[:, i]; node 0 gets minus the sum
         double g0[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int i = 0; i < 3; i++) {
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const double gi = s2 * fma(B[c][2], Gm[2][i], fma(B[c][1], Gm[1][i], B[c][0] * Gm[0][i]));
+                const double gi = fma(B[c][2], Gm[2][i], fma(B[c][1], Gm[1][i], B[c][0] * Gm[0][i]));
                 gpart[(e * 4 + i + 1) * 3 + c] = gi;
-                g0[c] -= gi;
+                g0[c] = i == 0 ? -gi : g0[c] - gi;
             }
         }
 #pragma unroll
@@ -185,12 +185,22 @@ __global__ void __launch_bounds__(256) k_node_reduce(const uint32_t* __restrict_
     grad[i * 3 + 2] = gz;
 }
 
-__global__ void k_sum_parts(const double* __restrict__ part, int64_t n, double* out)
+// Sum of the per-CTA energies in one fixed order: thread t adds parts t,
+// t + SUM_TPB, ... in turn, then a fixed shared-memory tree.
+constexpr int SUM_TPB = 1024;
+
+__global__ void __launch_bounds__(SUM_TPB) k_sum_parts(const double* __restrict__ part, int64_t n, double* out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double red[SUM_TPB];
     double s = 0.0;
-    for (int64_t i = 0; i < n; i++) s += part[i];
-    *out = s;
+    for (int64_t i = threadIdx.x; i < n; i += SUM_TPB) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = SUM_TPB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 __global__ void k_node_keys(const int32_t* elems, int64_t T, uint64_t* keys, uint32_t* vals, uint32_t* cnt)
@@ -253,7 +263,7 @@ int launch_adjoint(const ef_plan* p, const double* nodes, const double* coeff, c
     k_adjoint_ned3<<<(unsigned)nb, ADJ_TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_elem2dof, u, v, p->T, p->d_adj_part,
                                                     gs, p->d_adj_jpart, p->d_status);
     if (gx) k_node_reduce<<<(unsigned)((p->V + 255) / 256), 256, 0, s>>>(p->d_node_off, p->d_node_inc, p->d_adj_part, p->V, gx);
-    if (J) k_sum_parts<<<1, 32, 0, s>>>(p->d_adj_jpart, nb, J);
+    if (J) k_sum_parts<<<1, SUM_TPB, 0, s>>>(p->d_adj_jpart, nb, J);
     EF_CUDA(cudaGetLastError());
     return EF_OK;
 }
