@@ -170,6 +170,16 @@ int ef_plan_topology(const ef_plan* plan, int32_t* d_elem2dof, uint8_t* d_signbi
 int ef_assemble(const ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
                 void* stream);
 
+/* Assembly with separate element coefficients for the two matrices: K_K
+ * weighted by d_coeff_K[e] and M_K by d_coeff_M[e] (n_elems doubles each, or
+ * NULL = 1), e.g. 1/mu and kappa of the eddy-current problem (Sec. 4.2,
+ * curl 1/mu curl E + kappa E). Runs the two-pass kernels of
+ * ef_assemble_two_pass whatever schedule the plan has selected; with equal
+ * coefficient arrays the values are those of ef_assemble bit for bit.
+ * Asynchronous; allocates nothing; capturable. */
+int ef_assemble2(const ef_plan* plan, const double* d_nodes, const double* d_coeff_K, const double* d_coeff_M,
+                 double* d_Kval, double* d_Mval, void* stream);
+
 /* Same sums as ef_assemble, in two separate kernels: an element kernel writes
  * every local matrix to plan scratch, then one thread per upper nonzero sums
  * its contributions. Same values bit for bit (same summation order). */

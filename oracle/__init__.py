@@ -98,6 +98,8 @@ def _load():
         lib.ora_topology.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.POINTER(_Result)]
         lib.ora_assemble.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, C.c_int, C.c_int,
                                      C.POINTER(_Result)]
+        lib.ora_assemble2.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P, C.c_int, C.c_int,
+                                      C.POINTER(_Result)]
         lib.ora_adjoint.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P, P, C.c_int, C.c_int,
                                     P, P, P]
         _lib = lib
@@ -167,6 +169,22 @@ def assemble(kind: int, dim: int, nodes, elems, coeff=None, rule: int = 0, n: in
     res = _Result()
     st = lib.ora_assemble(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), _ptr(coeff),
                           rule, n, C.byref(res))
+    if st:
+        raise OracleError(st)
+    try:
+        return _unpack(res, True)
+    finally:
+        lib.ora_free(C.byref(res))
+
+
+def assemble2(kind: int, dim: int, nodes, elems, coeff_K=None, coeff_M=None, rule: int = 0, n: int = 0) -> dict:
+    """Assembly with K scaled by coeff_K and M by coeff_M (None: unit)."""
+    lib = _load()
+    nodes, elems, coeff_K = _prep(nodes, elems, coeff_K)
+    coeff_M = None if coeff_M is None else np.ascontiguousarray(coeff_M, dtype=np.float64)
+    res = _Result()
+    st = lib.ora_assemble2(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), _ptr(coeff_K),
+                           _ptr(coeff_M), rule, n, C.byref(res))
     if st:
         raise OracleError(st)
     try:

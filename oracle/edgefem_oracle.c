@@ -741,9 +741,12 @@ int ora_topology(int kind, int dim, int64_t V, const double* nodes, int64_t T, c
 }
 
 /* Full assembly: topology, signs, pattern, and K / M values by quadrature
- * rule (rule, n). coeff may be NULL (unit coefficient). */
-int ora_assemble(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems,
-                 const double* coeff, int rule, int n, ora_result* out)
+ * rule (rule, n), K scaled by coeff_K and M by coeff_M (either may be NULL:
+ * unit coefficient). With two different arrays the local matrices are
+ * evaluated once per coefficient and K taken from the first, M from the
+ * second (the matrices are linear in the coefficient). */
+int ora_assemble2(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems,
+                  const double* coeff_K, const double* coeff_M, int rule, int n, ora_result* out)
 {
     static qrule q;
     int st = ora_topology(kind, dim, V, nodes, T, elems, out);
@@ -772,7 +775,11 @@ int ora_assemble(int kind, int dim, int64_t V, const double* nodes, int64_t T, c
         double P[4][3], s[6], Kl[6][6], Ml[6][6];
         gather_points(dim, nodes, elems + e * nv, P);
         for (int k = 0; k < nl; k++) s[k] = out->sign[e * nl + k];
-        st = local_matrices_d(kind, dim, P, s, coeff ? coeff[e] : 1.0, &q, Kl, Ml);
+        st = local_matrices_d(kind, dim, P, s, coeff_K ? coeff_K[e] : 1.0, &q, Kl, Ml);
+        if (!st && coeff_M != coeff_K) {
+            double K2[6][6];
+            st = local_matrices_d(kind, dim, P, s, coeff_M ? coeff_M[e] : 1.0, &q, K2, Ml);
+        }
         if (st) {
             ora_free(out);
             return st;
@@ -791,6 +798,13 @@ int ora_assemble(int kind, int dim, int64_t V, const double* nodes, int64_t T, c
             }
     }
     return ORA_OK;
+}
+
+/* One coefficient for both matrices. */
+int ora_assemble(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems,
+                 const double* coeff, int rule, int n, ora_result* out)
+{
+    return ora_assemble2(kind, dim, V, nodes, T, elems, coeff, coeff, rule, n, out);
 }
 
 /*

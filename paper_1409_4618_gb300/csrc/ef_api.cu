@@ -411,6 +411,17 @@ int ef_assemble(const ef_plan* plan, const double* d_nodes, const double* d_coef
     return st;
 }
 
+int ef_assemble2(const ef_plan* plan, const double* d_nodes, const double* d_coeff_K, const double* d_coeff_M,
+                 double* d_Kval, double* d_Mval, void* stream)
+{
+    EF_TRY(assemble_checks(plan, d_nodes, d_Kval, d_Mval));
+    cudaStream_t s = (cudaStream_t)stream;
+    profile_begin(plan, s);
+    const int st = launch_two_pass2(plan, d_nodes, d_coeff_K, d_coeff_M, d_Kval, d_Mval, s);
+    profile_end(plan, s);
+    return st;
+}
+
 int ef_plan_profile(ef_plan* plan, int max_calls)
 {
     if (!plan || max_calls < 0) return EF_ERR_ARG;

@@ -38,7 +38,8 @@ constexpr int TPB = 256;
 template <int VAR>
 __global__ void __launch_bounds__(TPB, 3) k_element_local(const int32_t* __restrict__ elems,
                                                        const double* __restrict__ nodes,
-                                                       const double* __restrict__ coeff,
+                                                       const double* __restrict__ coeffK,
+                                                       const double* __restrict__ coeffM,
                                                        const uint32_t* __restrict__ inv, int64_t e0, int64_t e1,
                                                        int64_t T, double* __restrict__ list, int* status)
 {
@@ -46,8 +47,9 @@ __global__ void __launch_bounds__(TPB, 3) k_element_local(const int32_t* __restr
     const int64_t e = e0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (e >= e1) return;
     double Kq[E::NP], Mq[E::NP];
-    const double sigma = coeff ? __ldg(coeff + e) : 1.0;
-    if (compute_element<VAR>(elems, nodes, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
+    const double sigmaK = coeffK ? __ldg(coeffK + e) : 1.0;
+    const double sigmaM = coeffM == coeffK ? sigmaK : (coeffM ? __ldg(coeffM + e) : 1.0);
+    if (compute_element<VAR>(elems, nodes, sigmaK, sigmaM, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
     const int64_t nK = (int64_t)E::NP * T;
 #pragma unroll
     for (int q = 0; q < E::NP; q++) {
@@ -166,16 +168,16 @@ __global__ void k_count_keys(const uint32_t* seg, const uint32_t* list, int64_t 
     vals[i] = u;
 }
 
-int element_range(const ef_plan* p, const double* nodes, const double* coeff, int64_t e0, int64_t e1,
+int element_range(const ef_plan* p, const double* nodes, const double* cK, const double* cM, int64_t e0, int64_t e1,
                   cudaStream_t s)
 {
     if (e1 <= e0) return EF_OK;
     const unsigned grid = (unsigned)((e1 - e0 + TPB - 1) / TPB);
     switch (p->variant) {
-        case RT2: k_element_local<RT2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        case NED2: k_element_local<NED2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        case RT3: k_element_local<RT3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        default: k_element_local<NED3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, coeff, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT2: k_element_local<RT2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case NED2: k_element_local<NED2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT3: k_element_local<RT3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        default: k_element_local<NED3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
     }
     EF_CUDA(cudaGetLastError());
     return EF_OK;
@@ -317,17 +319,23 @@ int launch_two_pass_chunk(const ef_plan* p, int c, const double* nodes, const do
     if (c < 0 || c >= p->pc_chunks) return EF_ERR_ARG;
     const int64_t e0 = (int64_t)c * p->pc_chunk;
     const int64_t e1 = e0 + p->pc_chunk < p->T ? e0 + p->pc_chunk : p->T;
-    EF_TRY(element_range(p, nodes, coeff, e0, e1, s));
+    EF_TRY(element_range(p, nodes, coeff, coeff, e0, e1, s));
     return scatter_range(p, p->pc_woff[c], p->pc_woff[c + 1], K, M, s);
+}
+
+int launch_two_pass2(const ef_plan* p, const double* nodes, const double* coeffK, const double* coeffM, double* K,
+                     double* M, cudaStream_t s)
+{
+    if (p->T == 0) return EF_OK;
+    EF_TRY(element_range(p, nodes, coeffK, coeffM, 0, p->T, s));
+    profile_mid(p, s);
+    return scatter_range(p, 0, p->U, K, M, s);
 }
 
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M,
                     cudaStream_t s)
 {
-    if (p->T == 0) return EF_OK;
-    EF_TRY(element_range(p, nodes, coeff, 0, p->T, s));
-    profile_mid(p, s);
-    return scatter_range(p, 0, p->U, K, M, s);
+    return launch_two_pass2(p, nodes, coeff, coeff, K, M, s);
 }
 
 }  // namespace ef

@@ -30,11 +30,12 @@ __device__ __forceinline__ void load_ids(const int32_t* __restrict__ elems, int6
     }
 }
 
-// Signed local K, M upper triangles of element e times sigma; true if degenerate.
+// Signed local K, M upper triangles of element e, K times sigmaK and M times
+// sigmaM; true if degenerate.
 template <int VAR>
 __device__ __forceinline__ bool compute_element(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
-                                                double sigma, int64_t e, double (&Kq)[ElemTraits<VAR>::NP],
-                                                double (&Mq)[ElemTraits<VAR>::NP])
+                                                double sigmaK, double sigmaM, int64_t e,
+                                                double (&Kq)[ElemTraits<VAR>::NP], double (&Mq)[ElemTraits<VAR>::NP])
 {
     using E = ElemTraits<VAR>;
     int32_t g[E::NV];
@@ -47,16 +48,16 @@ __device__ __forceinline__ bool compute_element(const int32_t* __restrict__ elem
 #pragma unroll
             for (int c = 0; c < 3; c++) p[a][c] = __ldg(nodes + (int64_t)g[a] * 3 + c);
         if constexpr (VAR == NED3)
-            return ned3_local(p, sigma, neg, Kq, Mq);
+            return ned3_local(p, sigmaK, sigmaM, neg, Kq, Mq);
         else
-            return rt3_local(p, sigma, neg, Kq, Mq);
+            return rt3_local(p, sigmaK, sigmaM, neg, Kq, Mq);
     } else {
         double p[3][2];
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int c = 0; c < 2; c++) p[a][c] = __ldg(nodes + (int64_t)g[a] * 2 + c);
-        return tri_local<VAR == NED2 ? 2 : 0>(p, sigma, neg, Kq, Mq);
+        return tri_local<VAR == NED2 ? 2 : 0>(p, sigmaK, sigmaM, neg, Kq, Mq);
     }
 }
 

@@ -2,7 +2,10 @@
 // kernels of the two-pass and fused paths.
 //
 // Each function returns the upper triangle (k <= l, row-major) of the
-// signed local K and M of one element, times its coefficient sigma:
+// signed local K and M of one element, K times the element's coefficient
+// sigmaK and M times sigmaM (the same sigma in the paper's assembly; the
+// eddy-current problem of Sec. 4.2 weights K by 1/mu and M by kappa). Below,
+// sigma stands for the coefficient of the matrix in question:
 //
 //   RT0 (Eq. RT0local2 with Piola map RT0piola): with eta_k = x - p_opp(k)
 //   (Sec. 2.1, the opposite vertex of DOF k), B eta_k(xhat) = x - P_a, so
@@ -90,8 +93,8 @@ __device__ __forceinline__ bool not_positive(double x)
 }
 
 // ---- 3D Nedelec: 21 + 21 upper entries ---------------------------------------
-__device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma, uint32_t neg, double (&Kq)[21],
-                                           double (&Mq)[21])
+__device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigmaK, double sigmaM, uint32_t neg,
+                                           double (&Kq)[21], double (&Mq)[21])
 {
     const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
     const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
@@ -115,10 +118,10 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     const double adet = fabs(fma(e1z, cz, fma(e1y, cy, e1x * cx)));
     const bool bad = not_positive(adet);
     const double r = 1.0 / adet;
-    const double sr = sigma * r;
+    const double srK = sigmaK * r, srM = sigmaM * r;
 
     // K_kl = (2 sigma / (3|det|)) w_k . w_l
-    const double cK = sr * (2.0 / 3.0);
+    const double cK = srK * (2.0 / 3.0);
     const double h11 = cK * H11, h22 = cK * H22, h33 = cK * H33, h12 = cK * H12, h13 = cK * H13, h23 = cK * H23;
     const double k03 = h33 - h23, k04 = h13 - h12, k05 = h23 - h22;
     const double k13 = h13 - h33, k14 = h11 - h13, k15 = h12 - h23;
@@ -134,7 +137,7 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     // o_j the two other pairs); edges sharing node s with other ends u, v:
     // +-(2 S_s - (p_uv + o(uv))); disjoint edges (a,b), (c,d): p_ad + p_bc -
     // p_ac - p_bd, a difference of two o's. 41 operations after the scaling.
-    const double cM = sr * (1.0 / 120.0);
+    const double cM = srM * (1.0 / 120.0);
     const double g11 = cM * A11, g22 = cM * A22, g33 = cM * A33, g12 = cM * A12, g13 = cM * A13, g23 = cM * A23;
     const double p01 = g11 + g12 + g13, p02 = g12 + g22 + g23, p03 = g13 + g23 + g33;   // p12 = -g12, ...
     const double S0 = p01 + p02 + p03;
@@ -188,8 +191,8 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
 }
 
 // ---- 3D RT0: 10 + 10 upper entries (DOF k <-> opposite vertex 3-k) ---------
-__device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigma, uint32_t neg, double (&Kq)[10],
-                                          double (&Mq)[10])
+__device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigmaK, double sigmaM, uint32_t neg,
+                                          double (&Kq)[10], double (&Mq)[10])
 {
     const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
     const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
@@ -204,11 +207,11 @@ __device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigma,
     const double det = fma(e1z, cz, fma(e1y, cy, e1x * cx));
     const bool bad = not_positive(fabs(det));
     const double r = 1.0 / fabs(det);
-    const double sr = sigma * r;
+    const double srK = sigmaK * r, srM = sigmaM * r;
     // M: sigma/(120|det|) [c0 - 5 (S.y_a + S.y_b) + 20 y_a.y_b]
     const double r1 = H11 + H12 + H13, r2 = H12 + H22 + H23, r3 = H13 + H23 + H33;
     const double c0 = (r1 + r2 + r3) + (H11 + H22 + H33);
-    const double cM = sr * (1.0 / 120.0);
+    const double cM = srM * (1.0 / 120.0);
     const double m5 = -5.0 * cM, m20 = 20.0 * cM;
     const double c0s = c0 * cM;
     const double q1 = r1 * m5, q2 = r2 * m5, q3 = r3 * m5;
@@ -225,7 +228,7 @@ __device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigma,
     Mq[7] = fma(m20, H11, t1 + q1);
     Mq[8] = t1;
     Mq[9] = c0s;
-    const double kv = sr * 1.5;   // (div eta)^2 |Khat| = 9/6
+    const double kv = srK * 1.5;   // (div eta)^2 |Khat| = 9/6
     int q = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++)
@@ -240,8 +243,8 @@ __device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigma,
 
 // ---- 2D RT0 (VAR 0) and 2D Nedelec (VAR 2): 6 + 6 upper entries ------------
 template <int VAR>
-__device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigma, uint32_t neg, double (&Kq)[6],
-                                          double (&Mq)[6])
+__device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigmaK, double sigmaM, uint32_t neg,
+                                          double (&Kq)[6], double (&Mq)[6])
 {
     const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1];
     const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1];
@@ -249,8 +252,8 @@ __device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigma,
     const double det = fma(e1x, e2y, -(e1y * e2x));
     const bool bad = not_positive(fabs(det));
     const double r = 1.0 / fabs(det);
-    const double sr = sigma * r;
-    const double cM = sr * (1.0 / 24.0);
+    const double srK = sigmaK * r, srM = sigmaM * r;
+    const double cM = srM * (1.0 / 24.0);
     if (VAR == 0) {
         // RT0: sigma/(24|det|) [c0 - 4 (S.y_a + S.y_b) + 12 y_a.y_b], DOF k <-> vertex k
         const double r1 = H11 + H12, r2 = H12 + H22;
@@ -277,7 +280,7 @@ __device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigma,
         Mq[4] = fma(-2.0, g12, g01 - g00 + g02);
         d = g00 + g11 - g01; Mq[5] = d + d;
     }
-    const double kv = sr * 2.0;   // (div eta)^2 |Khat| = 4/2 (RT); curl^2 |Khat| = 4/2 (Ned)
+    const double kv = srK * 2.0;   // (div eta)^2 |Khat| = 4/2 (RT); curl^2 |Khat| = 4/2 (Ned)
     int q = 0;
 #pragma unroll
     for (int k = 0; k < 3; k++)

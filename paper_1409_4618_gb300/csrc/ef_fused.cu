@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(BE) k_fused(const int32_t* __restrict__ elems,
     if (e < T) {
         double Kq[E::NP], Mq[E::NP];
         const double sigma = coeff ? __ldg(coeff + e) : 1.0;
-        if (compute_element<VAR>(elems, nodes, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
+        if (compute_element<VAR>(elems, nodes, sigma, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
 #pragma unroll
         for (int q = 0; q < E::NP; q++) {
             smK[q * BE + threadIdx.x] = Kq[q];

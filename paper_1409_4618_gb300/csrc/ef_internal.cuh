@@ -159,6 +159,9 @@ int build_fused_block(ef_plan* p, int BE, cudaStream_t s);
 bool fused_block_supported(int BE);
 int build_adjoint(ef_plan* p, cudaStream_t s);
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);
+// Two-pass kernels with K weighted by coeffK and M by coeffM (NULL: 1).
+int launch_two_pass2(const ef_plan* p, const double* nodes, const double* coeffK, const double* coeffM, double* K,
+                     double* M, cudaStream_t s);
 // Element chunk c of the work order and the sums it completes.
 int launch_two_pass_chunk(const ef_plan* p, int c, const double* nodes, const double* coeff, double* K, double* M,
                           cudaStream_t s);

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
                 const double* coeff = nodes0 ? coeff0 : d.coeff;
                 double Kq[E::NP], Mq[E::NP];
                 const double sigma = coeff ? __ldg(coeff + e) : 1.0;
-                if (compute_element<VAR>(d.elems, nodes, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
+                if (compute_element<VAR>(d.elems, nodes, sigma, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
                 const int64_t nK = (int64_t)E::NP * d.T;
 #pragma unroll
                 for (int q = 0; q < E::NP; q++) {

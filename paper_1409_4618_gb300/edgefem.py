@@ -96,6 +96,7 @@ def load():
             "ef_plan_topology": ([P, P, P, P, P], I),
             "ef_assemble": ([P, P, P, P, P, P], I),
             "ef_assemble_two_pass": ([P, P, P, P, P, P], I),
+            "ef_assemble2": ([P, P, P, P, P, P, P], I),
             "ef_assemble_host": ([P, P, P, P, P, P], I),
             "ef_assemble_noalloc": ([P, P, P, P, P, P], I),
             "ef_plan_check": ([P, P], I),
@@ -200,6 +201,12 @@ def ef_plan_topology(plan, elem2dof=None, signbits=None, dof2nodes=None, stream=
 def ef_assemble(plan, nodes, coeff, K, M, stream=None):
     _check(load().ef_assemble(plan, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
                               _dev(K, torch.float64, "K"), _dev(M, torch.float64, "M"), _stream_ptr(stream)))
+
+
+def ef_assemble2(plan, nodes, coeff_K, coeff_M, K, M, stream=None):
+    _check(load().ef_assemble2(plan, _dev(nodes, torch.float64, "nodes"), _dev(coeff_K, torch.float64, "coeff_K"),
+                               _dev(coeff_M, torch.float64, "coeff_M"), _dev(K, torch.float64, "K"),
+                               _dev(M, torch.float64, "M"), _stream_ptr(stream)))
 
 
 def ef_assemble_two_pass(plan, nodes, coeff, K, M, stream=None):
@@ -343,6 +350,12 @@ class Plan:
     def assemble_two_pass(self, nodes, coeff=None, K=None, M=None, stream=None):
         K, M = self._vals(K, M)
         ef_assemble_two_pass(self.handle, nodes, coeff, K, M, stream)
+        return K, M
+
+    def assemble2(self, nodes, coeff_K=None, coeff_M=None, K=None, M=None, stream=None):
+        """K weighted by coeff_K, M by coeff_M (e.g. 1/mu and kappa)."""
+        K, M = self._vals(K, M)
+        ef_assemble2(self.handle, nodes, coeff_K, coeff_M, K, M, stream)
         return K, M
 
     def assemble_host(self, nodes, coeff=None, K=None, M=None, stream=None):

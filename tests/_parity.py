@@ -35,7 +35,7 @@ def signbits_from_signs(sign: np.ndarray) -> np.ndarray:
     return bits
 
 
-def run_gpu(kind, dim, nodes, elems, coeff=None, path="default", check=True):
+def run_gpu(kind, dim, nodes, elems, coeff=None, path="default", check=True, coeff_M=None):
     import torch
 
     from paper_1409_4618_gb300 import edgefem as ef
@@ -46,7 +46,9 @@ def run_gpu(kind, dim, nodes, elems, coeff=None, path="default", check=True):
     tc = None if coeff is None else torch.from_numpy(np.ascontiguousarray(coeff)).to(dev)
     plan = ef.Plan(kind, dim, nodes.shape[0], te)
     try:
-        if path == "two_pass":
+        if coeff_M is not None:
+            K, M = plan.assemble2(tn, tc, torch.from_numpy(np.ascontiguousarray(coeff_M)).to(dev))
+        elif path == "two_pass":
             K, M = plan.assemble_two_pass(tn, tc)
         elif path.startswith("blocked"):
             plan.set_block(int(path[len("blocked"):]))

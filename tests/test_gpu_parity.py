@@ -188,6 +188,20 @@ def test_tuner_keeps_results_and_picks_a_schedule():
     plan.close()
 
 
+@pytest.mark.parametrize("name", ["ned2d_33_shuffled", "rt2d_37_shuffled", "ned3d_13_shuffled", "rt3d_13_shuffled"])
+def test_separate_coefficients(ora, name):
+    """ef_assemble2: K weighted by one coefficient array, M by another, against
+    the oracle's assemble2; with equal arrays, ef_assemble's bits."""
+    kind, dim, nodes, elems, coeff = _case(name)
+    cM = mg.log_uniform_coeff(77, elems.shape[0])
+    g = run_gpu(kind, dim, nodes, elems, coeff, coeff_M=cM)
+    compare(g, ora.assemble2(kind, dim, nodes, elems, coeff, cM))
+    same = run_gpu(kind, dim, nodes, elems, coeff, coeff_M=coeff.copy())
+    one = run_gpu(kind, dim, nodes, elems, coeff)
+    for key in ("K", "M"):
+        assert np.array_equal(same[key].view(np.uint64), one[key].view(np.uint64))
+
+
 def test_kernel_profile_events():
     """ef_plan_profile records the kernels of exactly the requested number of
     calls; the two-pass schedule reports both kernels, the one-launch queue

@@ -10,6 +10,9 @@
   constant field c has energy |Omega| |c|^2, kernel dimensions V-1 and E-V+1,
   invariance under local node order and element order, the 2D rotation
   identity M_Ned = M_RT and K_Ned = K_RT, linearity in the coefficient.
+* Separate coefficients for K and M (assemble2): K from the brute force with
+  the K coefficient, M from the brute force with the M coefficient; equal
+  arrays reproduce assemble() bit for bit.
 """
 import numpy as np
 import pytest
@@ -170,6 +173,27 @@ def test_coefficient_linearity(ora, kind, dim):
     r2 = ora.assemble(kind, dim, nodes, elems, 2.0 * c)
     for key in ("K", "M"):
         np.testing.assert_allclose(r2[key], 2.0 * r1[key], rtol=1e-15, atol=1e-300)
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_separate_coefficients(ora, kind, dim):
+    n = 3 if dim == 3 else 4
+    nodes, elems = _mesh(dim, n, 23)
+    T = elems.shape[0]
+    cK = mg.log_uniform_coeff(23, T)
+    cM = mg.log_uniform_coeff(24, T)
+    r = ora.assemble2(kind, dim, nodes, elems, cK, cM)
+    Kb, _, _ = brute_force(kind, dim, nodes, elems, cK, nq=5)
+    _, Mb, _ = brute_force(kind, dim, nodes, elems, cM, nq=5)
+    np.testing.assert_allclose(to_dense(r, "K"), Kb, rtol=0, atol=1e-13 * np.abs(Kb).max())
+    np.testing.assert_allclose(to_dense(r, "M"), Mb, rtol=0, atol=1e-13 * np.abs(Mb).max())
+    one = ora.assemble(kind, dim, nodes, elems, cK)
+    same = ora.assemble2(kind, dim, nodes, elems, cK, cK.copy())
+    for key in ("K", "M"):
+        np.testing.assert_array_equal(same[key], one[key])
+    unitM = ora.assemble2(kind, dim, nodes, elems, cK, None)
+    np.testing.assert_array_equal(unitM["K"], one["K"])
+    np.testing.assert_array_equal(unitM["M"], ora.assemble(kind, dim, nodes, elems, None)["M"])
 
 
 @pytest.mark.parametrize("kind,dim", CASES)
