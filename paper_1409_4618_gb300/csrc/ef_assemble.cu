@@ -96,28 +96,70 @@ __global__ void k_work_inv(const uint32_t* order, int64_t U, const uint32_t* seg
 
 // Work item i sums list[wseg[i] .. wseg[i+1]): the contributions of one upper
 // nonzero, contiguous and in ascending element order; consecutive items are
-// consecutive in the list, so a warp reads one contiguous run.
-__global__ void __launch_bounds__(TPB) k_scatter(int64_t w0, int64_t w1, const uint32_t* __restrict__ wseg,
+// consecutive in the list, so a warp reads one contiguous run. The items are
+// summed in the work order (descending count inside windows, so a warp's
+// loops have equal length) but stored in position order: a CTA owns the
+// aligned block of 256 work items [256 b, 256 b + 256) (only those in
+// [w0, w1) on this launch), keeps its sums in shared memory, and thread t
+// then writes the t-th item of the block in ascending (r, c) position, and
+// again in ascending (c, r) position (the plan's store orders). Stores of a
+// warp then fall on few, mostly adjacent sectors instead of 32 scattered
+// ones; scattered 8-byte stores are bound by the L2's transaction rate.
+__global__ void __launch_bounds__(TPB) k_scatter(int64_t w0, int64_t w1, int64_t U, const uint32_t* __restrict__ wseg,
                                                  const uint32_t* __restrict__ wpos_up,
                                                  const uint32_t* __restrict__ wpos_lo,
+                                                 const uint8_t* __restrict__ st_up, const uint8_t* __restrict__ st_lo,
                                                  const double* __restrict__ listK, const double* __restrict__ listM,
                                                  double* __restrict__ K, double* __restrict__ M)
 {
-    const int64_t i = w0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (i >= w1) return;
-    const uint32_t s0 = wseg[i], s1 = wseg[i + 1];
-    const uint32_t pu = wpos_up[i], pl = wpos_lo[i];
-    double k = listK[s0], m = listM[s0];
-    for (uint32_t s = s0 + 1; s < s1; s++) {
-        k += listK[s];
-        m += listM[s];
+    __shared__ double sk[TPB], sm[TPB];
+    __shared__ uint32_t su[TPB], sl[TPB];
+    const int64_t base = (w0 / TPB + blockIdx.x) * TPB;
+    const int t = threadIdx.x;
+    const int64_t i = base + t;
+    if (i >= w0 && i < w1) {
+        const uint32_t s0 = wseg[i], s1 = wseg[i + 1];
+        su[t] = wpos_up[i];
+        sl[t] = wpos_lo[i];
+        double k = listK[s0], m = listM[s0];
+        for (uint32_t s = s0 + 1; s < s1; s++) {
+            k += listK[s];
+            m += listM[s];
+        }
+        sk[t] = k;
+        sm[t] = m;
     }
-    K[pu] = k;
-    M[pu] = m;
-    if (pl != 0xffffffffu) {
-        K[pl] = k;
-        M[pl] = m;
+    __syncthreads();
+    if (base + t >= U) return;
+    int q = st_up[base + t];
+    if (base + q >= w0 && base + q < w1) {
+        const uint32_t p = su[q];
+        K[p] = sk[q];
+        M[p] = sm[q];
     }
+    q = st_lo[base + t];
+    if (base + q >= w0 && base + q < w1) {
+        const uint32_t p = sl[q];
+        if (p != 0xffffffffu) {
+            K[p] = sk[q];
+            M[p] = sm[q];
+        }
+    }
+}
+
+// Store-order keys: block of the work item, then its CSR position.
+__global__ void k_store_keys(const uint32_t* __restrict__ wpos, int64_t U, uint64_t* keys, uint32_t* vals)
+{
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= U) return;
+    keys[i] = ((uint64_t)(i / TPB) << 32) | wpos[i];
+    vals[i] = (uint32_t)(i % TPB);
+}
+
+__global__ void k_store_bytes(const uint32_t* __restrict__ vals, int64_t U, uint8_t* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i < U) out[i] = (uint8_t)vals[i];
 }
 
 // Latest completing chunk of every CSR row: row r is final once every upper
@@ -186,20 +228,22 @@ int element_range(const ef_plan* p, const double* nodes, const double* cK, const
 int scatter_range(const ef_plan* p, int64_t w0, int64_t w1, double* K, double* M, cudaStream_t s)
 {
     if (w1 <= w0) return EF_OK;
-    const unsigned grid = (unsigned)((w1 - w0 + TPB - 1) / TPB);
+    const unsigned grid = (unsigned)((w1 - 1) / TPB - w0 / TPB + 1);
     const double* lK = p->d_local;
     const double* lM = p->d_local + (int64_t)p->np * p->T;
-    k_scatter<<<grid, TPB, 0, s>>>(w0, w1, p->d_wseg, p->d_wpos_up, p->d_wpos_lo, lK, lM, K, M);
+    k_scatter<<<grid, TPB, 0, s>>>(w0, w1, p->U, p->d_wseg, p->d_wpos_up, p->d_wpos_lo, p->d_wst_up, p->d_wst_lo, lK,
+                                   lM, K, M);
     EF_CUDA(cudaGetLastError());
     return EF_OK;
 }
 
 void free_work_order(ef_plan* p)
 {
-    void* ptrs[] = {p->d_wseg, p->d_wpos_up, p->d_wpos_lo, p->d_inv};
+    void* ptrs[] = {p->d_wseg, p->d_wpos_up, p->d_wpos_lo, p->d_inv, p->d_wst_up, p->d_wst_lo};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     p->d_wseg = p->d_wpos_up = p->d_wpos_lo = p->d_inv = nullptr;
+    p->d_wst_up = p->d_wst_lo = nullptr;
 }
 
 }  // namespace
@@ -239,6 +283,7 @@ int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
     if (!ok(cudaMalloc((void**)&p->d_inv, n * 4)) || !ok(cudaMalloc((void**)&p->d_wseg, (U + 1) * 4)) ||
         !ok(cudaMalloc((void**)&p->d_wpos_up, U * 4)) || !ok(cudaMalloc((void**)&p->d_wpos_lo, U * 4)) ||
+        !ok(cudaMalloc((void**)&p->d_wst_up, U)) || !ok(cudaMalloc((void**)&p->d_wst_lo, U)) ||
         !ok(cudaMalloc((void**)&order, U * 4)) || !ok(cudaMalloc((void**)&keys, U * 8)) ||
         !ok(cudaMalloc((void**)&wcnt, U * 4)) || !ok(cudaMalloc((void**)&cnt, EF_MAX_CHUNKS * 4)) ||
         !ok(cudaMalloc(&tmp, tb)))
@@ -258,6 +303,18 @@ int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
     int64_t hpos[EF_MAX_CHUNKS] = {0};
     if (st == EF_OK) {
         k_work_inv<<<gu, TPB, 0, s>>>(order, U, p->d_seg, p->d_perm, p->d_wseg, p->d_inv);
+        // store orders of the sum (keys and wcnt are free scratch now)
+        const uint64_t kmax = ((uint64_t)((U - 1) / TPB) << 32) | 0xffffffffull;
+        k_store_keys<<<gu, TPB, 0, s>>>(p->d_wpos_up, U, keys, wcnt);
+        st = radix_sort_pairs(keys, wcnt, U, bits_for(kmax), tmp, s);
+        if (st == EF_OK) {
+            k_store_bytes<<<gu, TPB, 0, s>>>(wcnt, U, p->d_wst_up);
+            k_store_keys<<<gu, TPB, 0, s>>>(p->d_wpos_lo, U, keys, wcnt);
+            st = radix_sort_pairs(keys, wcnt, U, bits_for(kmax), tmp, s);
+        }
+        if (st == EF_OK) k_store_bytes<<<gu, TPB, 0, s>>>(wcnt, U, p->d_wst_lo);
+    }
+    if (st == EF_OK) {
         cudaMemcpyAsync(hc, cnt, EF_MAX_CHUNKS * 4, cudaMemcpyDeviceToHost, s);
         // CSR prefix that is final after each chunk (the scratch `order` and
         // `keys` are free again): rows' last chunks, first open row, position
