@@ -258,11 +258,13 @@ int ef_adjoint(const ef_plan* plan, const double* d_nodes, const double* d_coeff
 
 /*
  * A batch holds independent meshes of one kind and dimension, each with its
- * own plan and its own CSR. ef_batch_assemble assembles all of them in ONE
- * persistent kernel launch over (mesh, element tile) and (mesh, sum tile)
- * work; a sum tile starts once the element tiles it depends on are done (a
- * bounded wait; EF_ERR_TIMEOUT from ef_batch_check if a wait gave up). Values
- * are those of ef_assemble on each mesh, bit for bit.
+ * own plan and its own CSR. ef_batch_assemble assembles all of them either in
+ * ONE persistent kernel launch over (mesh, element tile) and (mesh, sum tile)
+ * work, where a sum tile starts once the element tiles it depends on are done
+ * (a bounded wait; EF_ERR_TIMEOUT from ef_batch_check if a wait gave up), or
+ * in two launches over all meshes (element kernel, then sum kernel), as the
+ * configuration says. Values are those of ef_assemble on each mesh, bit for
+ * bit.
  */
 typedef struct ef_batch ef_batch;
 
@@ -276,6 +278,8 @@ typedef struct {
     int32_t elem_ctas;       /* 0: every CTA takes tiles of both kinds from one interleaved queue;
                                 k in 1..3: in each group of 4 CTAs, k take only element tiles and
                                 4-k only sum tiles (two queues) */
+    int32_t two_launch;      /* 1: instead of the persistent launch, two launches over all meshes:
+                                the element kernel, then the sum kernel (the other fields unused) */
 } ef_batch_config_t;
 
 /* Build the per-mesh plans (as ef_plan_create for each). n_nodes, n_elems:
@@ -293,14 +297,16 @@ int ef_batch_pattern(const ef_batch* batch, int mesh, int64_t* d_rowptr, int32_t
  * Copies the pointer tables to the device and synchronises `stream`. */
 int ef_batch_bind(ef_batch* batch, const double* const* d_nodes, const double* const* d_coeff, double* const* d_K,
                   double* const* d_M, void* stream);
-/* One persistent launch assembling every mesh into its bound buffers.
- * Asynchronous, no allocation, no host synchronisation; capturable in a CUDA
- * graph. Calls that overlap on the GPU race. EF_ERR_ARG if nothing is bound. */
+/* Assemble every mesh into its bound buffers: one persistent launch, or two
+ * launches with two_launch set. Asynchronous, no allocation, no host
+ * synchronisation; capturable in a CUDA graph. Calls that overlap on the GPU
+ * race. EF_ERR_ARG if nothing is bound. */
 int ef_batch_assemble(const ef_batch* batch, void* stream);
 /* Autotuner: times each candidate schedule `reps` times on the bound buffers
- * (elements per tile 128/256, sum tiles 512/2048/8192 nonzeros, full or half
- * occupancy, dynamic or static, given or largest-first mesh order) and keeps
- * the fastest; writes it to *best (may be NULL). Overwrites the bound K, M. */
+ * (the two-launch form; the persistent launch with 128/256 elements per tile,
+ * 512/2048 nonzeros per sum tile, 0-2 element-only CTAs per four, dynamic or
+ * static tickets, given or largest-first mesh order) and keeps the fastest;
+ * writes it to *best (may be NULL). Overwrites the bound K, M. */
 int ef_batch_tune(ef_batch* batch, int reps, ef_batch_config_t* best, void* stream);
 int ef_batch_get_config(const ef_batch* batch, ef_batch_config_t* cfg);
 int ef_batch_set_config(ef_batch* batch, const ef_batch_config_t* cfg, void* stream);

@@ -24,8 +24,11 @@
 // The chunking of the work order (the chunk that completes each nonzero) is
 // what the persistent queue of ef_queue.cu interleaves; the kernels here are
 // the plain two-pass form (ef_assemble_two_pass).
+#include <type_traits>
+
 #include "ef_assemble.cuh"
 #include "ef_internal.cuh"
+#include "ef_queue.cuh"
 
 namespace ef {
 namespace {
@@ -36,16 +39,12 @@ constexpr int TPB = 256;
 // list: inv[q * T + e] = position of (element e, pair q). K values occupy
 // list[0, np T), M values list[np T, 2 np T).
 template <int VAR>
-__global__ void __launch_bounds__(TPB, 3) k_element_local(const int32_t* __restrict__ elems,
-                                                       const double* __restrict__ nodes,
-                                                       const double* __restrict__ coeffK,
-                                                       const double* __restrict__ coeffM,
-                                                       const uint32_t* __restrict__ inv, int64_t e0, int64_t e1,
-                                                       int64_t T, double* __restrict__ list, int* status)
+__device__ __forceinline__ void element_body(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
+                                             const double* __restrict__ coeffK, const double* __restrict__ coeffM,
+                                             const uint32_t* __restrict__ inv, int64_t e, int64_t T,
+                                             double* __restrict__ list, int* status)
 {
     using E = ElemTraits<VAR>;
-    const int64_t e = e0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (e >= e1) return;
     double Kq[E::NP], Mq[E::NP];
     const double sigmaK = coeffK ? __ldg(coeffK + e) : 1.0;
     const double sigmaM = coeffM == coeffK ? sigmaK : (coeffM ? __ldg(coeffM + e) : 1.0);
@@ -57,6 +56,50 @@ __global__ void __launch_bounds__(TPB, 3) k_element_local(const int32_t* __restr
         list[pos] = Kq[q];
         list[nK + pos] = Mq[q];
     }
+}
+
+template <int VAR>
+__global__ void __launch_bounds__(TPB, 3) k_element_local(const int32_t* __restrict__ elems,
+                                                       const double* __restrict__ nodes,
+                                                       const double* __restrict__ coeffK,
+                                                       const double* __restrict__ coeffM,
+                                                       const uint32_t* __restrict__ inv, int64_t e0, int64_t e1,
+                                                       int64_t T, double* __restrict__ list, int* status)
+{
+    const int64_t e = e0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (e >= e1) return;
+    element_body<VAR>(elems, nodes, coeffK, coeffM, inv, e, T, list, status);
+}
+
+// Mesh descriptor of CTA b of a batch launch into shared memory: blk_mesh[b]
+// is the CTA's mesh, blk_off[m] the first CTA of mesh m; the descriptor's
+// words are loaded by the first threads in parallel.
+__device__ __forceinline__ int64_t load_block_mesh(const QueueMesh* __restrict__ md,
+                                                   const uint32_t* __restrict__ blk_mesh,
+                                                   const int64_t* __restrict__ blk_off, QueueMesh& d, int64_t* first)
+{
+    constexpr int W = (int)(sizeof(QueueMesh) / 8);
+    static_assert(sizeof(QueueMesh) % 8 == 0, "descriptor of 8-byte words");
+    const uint32_t m = __ldg(blk_mesh + blockIdx.x);
+    if (threadIdx.x < W)
+        reinterpret_cast<uint64_t*>(&d)[threadIdx.x] = __ldg(reinterpret_cast<const uint64_t*>(md + m) + threadIdx.x);
+    if (threadIdx.x == W) *first = __ldg(blk_off + m);
+    __syncthreads();
+    return blockIdx.x - *first;
+}
+
+// The element kernel over every mesh of a batch: CTA b takes TPB elements of
+// mesh m, blocks of meshes one after the other (blk_off: prefix of blocks).
+template <int VAR>
+__global__ void __launch_bounds__(TPB, 3) k_batch_element(const QueueMesh* __restrict__ md,
+                                                       const uint32_t* __restrict__ blk_mesh,
+                                                       const int64_t* __restrict__ blk_off, int* status)
+{
+    __shared__ QueueMesh d;
+    __shared__ int64_t first;
+    const int64_t e = load_block_mesh(md, blk_mesh, blk_off, d, &first) * TPB + threadIdx.x;
+    if (e >= d.T) return;
+    element_body<VAR>(d.elems, d.nodes, d.coeff, d.coeff, d.inv, e, d.T, d.list, status);
 }
 
 __global__ void k_work_keys(const uint32_t* seg, const uint32_t* perm, int64_t U, int64_t T, int64_t chunk,
@@ -99,22 +142,26 @@ __global__ void k_work_inv(const uint32_t* order, int64_t U, const uint32_t* seg
 // consecutive in the list, so a warp reads one contiguous run. The items are
 // summed in the work order (descending count inside windows, so a warp's
 // loops have equal length) but stored in position order: a CTA owns the
-// aligned block of 256 work items [256 b, 256 b + 256) (only those in
-// [w0, w1) on this launch), keeps its sums in shared memory, and thread t
-// then writes the t-th item of the block in ascending (r, c) position, and
-// again in ascending (c, r) position (the plan's store orders). Stores of a
-// warp then fall on few, mostly adjacent sectors instead of 32 scattered
-// ones; scattered 8-byte stores are bound by the L2's transaction rate.
-__global__ void __launch_bounds__(TPB) k_scatter(int64_t w0, int64_t w1, int64_t U, const uint32_t* __restrict__ wseg,
-                                                 const uint32_t* __restrict__ wpos_up,
-                                                 const uint32_t* __restrict__ wpos_lo,
-                                                 const uint8_t* __restrict__ st_up, const uint8_t* __restrict__ st_lo,
-                                                 const double* __restrict__ listK, const double* __restrict__ listM,
-                                                 double* __restrict__ K, double* __restrict__ M)
+// aligned block of SB work items [SB b, SB b + SB) (only those in [w0, w1)
+// on this launch), keeps its sums in shared memory, and thread t then writes
+// the t-th item of the block in ascending (r, c) position, and again in
+// ascending (c, r) position (the plan's store orders). Stores of a warp then
+// fall on few, mostly adjacent sectors instead of 32 scattered ones;
+// scattered 8-byte stores are bound by the L2's transaction rate.
+constexpr int SB = 256;
+using StoreIdx = std::conditional_t<(SB <= 256), uint8_t, uint16_t>;
+
+// Sums of the aligned block [base, base + SB) of work items, those in
+// [w0, w1) only, stored in position order.
+__device__ __forceinline__ void scatter_body(int64_t base, int64_t w0, int64_t w1, int64_t U,
+                                             const uint32_t* __restrict__ wseg, const uint32_t* __restrict__ wpos_up,
+                                             const uint32_t* __restrict__ wpos_lo,
+                                             const StoreIdx* __restrict__ st_up, const StoreIdx* __restrict__ st_lo,
+                                             const double* __restrict__ listK, const double* __restrict__ listM,
+                                             double* __restrict__ K, double* __restrict__ M)
 {
-    __shared__ double sk[TPB], sm[TPB];
-    __shared__ uint32_t su[TPB], sl[TPB];
-    const int64_t base = (w0 / TPB + blockIdx.x) * TPB;
+    __shared__ double sk[SB], sm[SB];
+    __shared__ uint32_t su[SB], sl[SB];
     const int t = threadIdx.x;
     const int64_t i = base + t;
     if (i >= w0 && i < w1) {
@@ -147,19 +194,45 @@ __global__ void __launch_bounds__(TPB) k_scatter(int64_t w0, int64_t w1, int64_t
     }
 }
 
+__global__ void __launch_bounds__(SB) k_scatter(int64_t w0, int64_t w1, int64_t U, const uint32_t* __restrict__ wseg,
+                                                const uint32_t* __restrict__ wpos_up,
+                                                const uint32_t* __restrict__ wpos_lo,
+                                                const StoreIdx* __restrict__ st_up, const StoreIdx* __restrict__ st_lo,
+                                                const double* __restrict__ listK, const double* __restrict__ listM,
+                                                double* __restrict__ K, double* __restrict__ M)
+{
+    scatter_body((w0 / SB + blockIdx.x) * SB, w0, w1, U, wseg, wpos_up, wpos_lo, st_up, st_lo, listK, listM, K, M);
+}
+
+// The sum over every mesh of a batch: CTA b takes the SB-block of work items
+// b - blk_off[m] of mesh m.
+template <int NP>
+__global__ void __launch_bounds__(SB, 8) k_batch_scatter(const QueueMesh* __restrict__ md,
+                                                      const uint32_t* __restrict__ blk_mesh,
+                                                      const int64_t* __restrict__ blk_off)
+{
+    // the CTA's mesh descriptor in shared memory: read there where it is used
+    // instead of held in registers
+    __shared__ QueueMesh d;
+    __shared__ int64_t first;
+    const int64_t base = load_block_mesh(md, blk_mesh, blk_off, d, &first) * SB;
+    scatter_body(base, 0, d.U, d.U, d.wseg, d.wpos_up, d.wpos_lo, (const StoreIdx*)d.wst_up,
+                 (const StoreIdx*)d.wst_lo, d.list, d.list + (int64_t)NP * d.T, d.K, d.M);
+}
+
 // Store-order keys: block of the work item, then its CSR position.
 __global__ void k_store_keys(const uint32_t* __restrict__ wpos, int64_t U, uint64_t* keys, uint32_t* vals)
 {
     const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (i >= U) return;
-    keys[i] = ((uint64_t)(i / TPB) << 32) | wpos[i];
-    vals[i] = (uint32_t)(i % TPB);
+    keys[i] = ((uint64_t)(i / SB) << 32) | wpos[i];
+    vals[i] = (uint32_t)(i % SB);
 }
 
-__global__ void k_store_bytes(const uint32_t* __restrict__ vals, int64_t U, uint8_t* out)
+__global__ void k_store_index(const uint32_t* __restrict__ vals, int64_t U, StoreIdx* out)
 {
     const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (i < U) out[i] = (uint8_t)vals[i];
+    if (i < U) out[i] = (StoreIdx)vals[i];
 }
 
 // Latest completing chunk of every CSR row: row r is final once every upper
@@ -228,11 +301,11 @@ int element_range(const ef_plan* p, const double* nodes, const double* cK, const
 int scatter_range(const ef_plan* p, int64_t w0, int64_t w1, double* K, double* M, cudaStream_t s)
 {
     if (w1 <= w0) return EF_OK;
-    const unsigned grid = (unsigned)((w1 - 1) / TPB - w0 / TPB + 1);
+    const unsigned grid = (unsigned)((w1 - 1) / SB - w0 / SB + 1);
     const double* lK = p->d_local;
     const double* lM = p->d_local + (int64_t)p->np * p->T;
-    k_scatter<<<grid, TPB, 0, s>>>(w0, w1, p->U, p->d_wseg, p->d_wpos_up, p->d_wpos_lo, p->d_wst_up, p->d_wst_lo, lK,
-                                   lM, K, M);
+    k_scatter<<<grid, SB, 0, s>>>(w0, w1, p->U, p->d_wseg, p->d_wpos_up, p->d_wpos_lo, (const StoreIdx*)p->d_wst_up,
+                                  (const StoreIdx*)p->d_wst_lo, lK, lM, K, M);
     EF_CUDA(cudaGetLastError());
     return EF_OK;
 }
@@ -283,7 +356,7 @@ int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
     if (!ok(cudaMalloc((void**)&p->d_inv, n * 4)) || !ok(cudaMalloc((void**)&p->d_wseg, (U + 1) * 4)) ||
         !ok(cudaMalloc((void**)&p->d_wpos_up, U * 4)) || !ok(cudaMalloc((void**)&p->d_wpos_lo, U * 4)) ||
-        !ok(cudaMalloc((void**)&p->d_wst_up, U)) || !ok(cudaMalloc((void**)&p->d_wst_lo, U)) ||
+        !ok(cudaMalloc(&p->d_wst_up, U * sizeof(StoreIdx))) || !ok(cudaMalloc(&p->d_wst_lo, U * sizeof(StoreIdx))) ||
         !ok(cudaMalloc((void**)&order, U * 4)) || !ok(cudaMalloc((void**)&keys, U * 8)) ||
         !ok(cudaMalloc((void**)&wcnt, U * 4)) || !ok(cudaMalloc((void**)&cnt, EF_MAX_CHUNKS * 4)) ||
         !ok(cudaMalloc(&tmp, tb)))
@@ -304,15 +377,15 @@ int build_work_order(ef_plan* p, int nchunks, cudaStream_t s)
     if (st == EF_OK) {
         k_work_inv<<<gu, TPB, 0, s>>>(order, U, p->d_seg, p->d_perm, p->d_wseg, p->d_inv);
         // store orders of the sum (keys and wcnt are free scratch now)
-        const uint64_t kmax = ((uint64_t)((U - 1) / TPB) << 32) | 0xffffffffull;
+        const uint64_t kmax = ((uint64_t)((U - 1) / SB) << 32) | 0xffffffffull;
         k_store_keys<<<gu, TPB, 0, s>>>(p->d_wpos_up, U, keys, wcnt);
         st = radix_sort_pairs(keys, wcnt, U, bits_for(kmax), tmp, s);
         if (st == EF_OK) {
-            k_store_bytes<<<gu, TPB, 0, s>>>(wcnt, U, p->d_wst_up);
+            k_store_index<<<gu, TPB, 0, s>>>(wcnt, U, (StoreIdx*)p->d_wst_up);
             k_store_keys<<<gu, TPB, 0, s>>>(p->d_wpos_lo, U, keys, wcnt);
             st = radix_sort_pairs(keys, wcnt, U, bits_for(kmax), tmp, s);
         }
-        if (st == EF_OK) k_store_bytes<<<gu, TPB, 0, s>>>(wcnt, U, p->d_wst_lo);
+        if (st == EF_OK) k_store_index<<<gu, TPB, 0, s>>>(wcnt, U, (StoreIdx*)p->d_wst_lo);
     }
     if (st == EF_OK) {
         cudaMemcpyAsync(hc, cnt, EF_MAX_CHUNKS * 4, cudaMemcpyDeviceToHost, s);
@@ -369,6 +442,36 @@ int default_pipeline_chunks(const ef_plan* p)
 }
 
 void release_work_order(ef_plan* p) { free_work_order(p); }
+
+// Batch in two launches: every mesh's element kernel, then every mesh's sums.
+int launch_batch_two_pass(int variant, const QueueMesh* d_mesh, const uint32_t* d_emesh, const int64_t* d_eblk,
+                          int64_t n_eblk, const uint32_t* d_smesh, const int64_t* d_sblk, int64_t n_sblk, int* status,
+                          cudaStream_t s)
+{
+    if (n_eblk > 0) {
+        const unsigned g = (unsigned)n_eblk;
+        switch (variant) {
+            case RT2: k_batch_element<RT2><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+            case NED2: k_batch_element<NED2><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+            case RT3: k_batch_element<RT3><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+            default: k_batch_element<NED3><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+        }
+    }
+    if (n_sblk > 0) {
+        const unsigned g = (unsigned)n_sblk;
+        switch (variant) {
+            case RT2:
+            case NED2: k_batch_scatter<ElemTraits<RT2>::NP><<<g, SB, 0, s>>>(d_mesh, d_smesh, d_sblk); break;
+            case RT3: k_batch_scatter<ElemTraits<RT3>::NP><<<g, SB, 0, s>>>(d_mesh, d_smesh, d_sblk); break;
+            default: k_batch_scatter<ElemTraits<NED3>::NP><<<g, SB, 0, s>>>(d_mesh, d_smesh, d_sblk); break;
+        }
+    }
+    EF_CUDA(cudaGetLastError());
+    return EF_OK;
+}
+
+int64_t element_blocks(int64_t T) { return (T + TPB - 1) / TPB; }
+int64_t sum_blocks(int64_t U) { return (U + SB - 1) / SB; }
 
 int launch_two_pass_chunk(const ef_plan* p, int c, const double* nodes, const double* coeff, double* K, double* M,
                           cudaStream_t s)

@@ -66,6 +66,7 @@ int ef_batch_create(int kind, int dim, int n_meshes, const int64_t* n_nodes, con
         b->queue.cfg.elems_per_tile = 128;
         b->queue.cfg.sum_tile = 2048;
         b->queue.cfg.elem_ctas = 0;
+        b->queue.cfg.two_launch = 1;
         b->queue.cfg.ctas_per_sm = queue_max_ctas_per_sm(b->variant, 128);
         if (b->queue.cfg.ctas_per_sm < 1) st = EF_ERR_CUDA;
     }
@@ -131,6 +132,7 @@ int ef_batch_set_config(ef_batch* b, const ef_batch_config_t* cfg, void* stream)
     if (!b || !cfg) return EF_ERR_ARG;
     if (cfg->elems_per_tile != 128 && cfg->elems_per_tile != 256) return EF_ERR_ARG;
     if (cfg->elem_ctas < 0 || cfg->elem_ctas > 3) return EF_ERR_ARG;
+    if (cfg->two_launch != 0 && cfg->two_launch != 1) return EF_ERR_ARG;
     if (cfg->sum_tile < cfg->elems_per_tile || cfg->sum_tile > (1 << 20)) return EF_ERR_ARG;
     const int maxc = queue_max_ctas_per_sm(b->variant, cfg->elems_per_tile);
     if (cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > maxc) return EF_ERR_ARG;
@@ -151,6 +153,30 @@ int ef_batch_tune(ef_batch* b, int reps, ef_batch_config_t* best_out, void* stre
     const int tiles[2] = {128, 256};
     const int sums[2] = {512, 2048};
     int st = EF_OK;
+    auto time_config = [&](const ef_batch_config_t& c) {
+        b->queue.cfg = c;
+        if ((st = queue_build(&b->queue, b->plans, s)) != EF_OK) return;
+        if ((st = queue_launch(&b->queue, QueueArgs(), s)) != EF_OK) return;   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == EF_OK; r++) st = queue_launch(&b->queue, QueueArgs(), s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = EF_ERR_CUDA;
+            return;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    };
+    {
+        ef_batch_config_t c = b->queue.cfg;
+        c.two_launch = 1;
+        time_config(c);
+    }
     for (int ti = 0; ti < 2 && st == EF_OK; ti++) {
         const int maxc = queue_max_ctas_per_sm(b->variant, tiles[ti]);
         for (int su = 0; su < 2 && st == EF_OK; su++)
@@ -163,25 +189,10 @@ int ef_batch_tune(ef_batch* b, int reps, ef_batch_config_t* best_out, void* stre
                         c.dynamic = dyn;
                         c.largest_first = lf;
                         c.elem_ctas = ec;
+                        c.two_launch = 0;
                         c.ctas_per_sm = maxc;
                         if (c.ctas_per_sm < 1) continue;
-                        b->queue.cfg = c;
-                        if ((st = queue_build(&b->queue, b->plans, s)) != EF_OK) break;
-                        if ((st = queue_launch(&b->queue, QueueArgs(), s)) != EF_OK) break;   // warm-up
-                        cudaEventRecord(e0, s);
-                        for (int r = 0; r < reps && st == EF_OK; r++) st = queue_launch(&b->queue, QueueArgs(), s);
-                        cudaEventRecord(e1, s);
-                        if (cudaEventSynchronize(e1) != cudaSuccess) {
-                            st = EF_ERR_CUDA;
-                            break;
-                        }
-                        float ms = 0;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        ms /= reps;
-                        if (ms < best_ms) {
-                            best_ms = ms;
-                            best = c;
-                        }
+                        time_config(c);
                     }
     }
     cudaEventDestroy(e0);

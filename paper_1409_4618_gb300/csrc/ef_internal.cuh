@@ -101,8 +101,8 @@ struct ef_plan {
                           //   chunk, then descending contribution count inside 256-windows of u)
     uint32_t* d_wpos_up;  // U: CSR position of (r, c) of each work item
     uint32_t* d_wpos_lo;  // U: CSR position of (c, r), or 0xffffffff
-    uint8_t* d_wst_up;    // U: per block of 256 work items, the items in ascending (r, c) position
-    uint8_t* d_wst_lo;    // U: per block of 256 work items, the items in ascending (c, r) position
+    void* d_wst_up;       // U: per block of sum items (ef_assemble.cu), the items in ascending (r, c) position
+    void* d_wst_lo;       // U: per block of sum items, the items in ascending (c, r) position
     double* d_local;      // 2 * np * T: contribution list (K then M values) of the two-pass paths
     int* d_status;        // device status word
 

@@ -289,6 +289,44 @@ int queue_build(Queue* q, const std::vector<ef_plan*>& plans, cudaStream_t s)
     q->nseg = (int)segs.size();
     q->ntiles = off;
     q->nctr = N;
+    // two-launch schedule: element and sum blocks of the meshes, in mesh order
+    {
+        std::vector<int64_t> eb(n + 1, 0), sb(n + 1, 0);
+        for (int m = 0; m < n; m++) {
+            eb[m + 1] = eb[m] + element_blocks(plans[m]->T);
+            sb[m + 1] = sb[m] + sum_blocks(plans[m]->U);
+        }
+        if (q->nmesh < n || !q->d_eblk) {
+            if (q->d_eblk) cudaFree(q->d_eblk);
+            if (q->d_sblk) cudaFree(q->d_sblk);
+            q->d_eblk = q->d_sblk = nullptr;
+            EF_CUDA(cudaMalloc((void**)&q->d_eblk, sizeof(int64_t) * (n + 1)));
+            EF_CUDA(cudaMalloc((void**)&q->d_sblk, sizeof(int64_t) * (n + 1)));
+        }
+        q->nmesh = n;
+        q->n_eblk = eb[n];
+        q->n_sblk = sb[n];
+        std::vector<uint32_t> em((size_t)(eb[n] > 0 ? eb[n] : 1)), sm((size_t)(sb[n] > 0 ? sb[n] : 1));
+        for (int m = 0; m < n; m++) {
+            for (int64_t b = eb[m]; b < eb[m + 1]; b++) em[b] = (uint32_t)m;
+            for (int64_t b = sb[m]; b < sb[m + 1]; b++) sm[b] = (uint32_t)m;
+        }
+        if (q->cap_eblk < (int64_t)em.size() || q->cap_sblk < (int64_t)sm.size()) {
+            if (q->d_emesh) cudaFree(q->d_emesh);
+            if (q->d_smesh) cudaFree(q->d_smesh);
+            q->d_emesh = q->d_smesh = nullptr;
+            q->cap_eblk = q->cap_sblk = 0;
+            EF_CUDA(cudaMalloc((void**)&q->d_emesh, sizeof(uint32_t) * em.size()));
+            EF_CUDA(cudaMalloc((void**)&q->d_smesh, sizeof(uint32_t) * sm.size()));
+            q->cap_eblk = (int64_t)em.size();
+            q->cap_sblk = (int64_t)sm.size();
+        }
+        EF_CUDA(cudaMemcpyAsync(q->d_eblk, eb.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+        EF_CUDA(cudaMemcpyAsync(q->d_sblk, sb.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+        EF_CUDA(cudaMemcpyAsync(q->d_emesh, em.data(), sizeof(uint32_t) * em.size(), cudaMemcpyHostToDevice, s));
+        EF_CUDA(cudaMemcpyAsync(q->d_smesh, sm.data(), sizeof(uint32_t) * sm.size(), cudaMemcpyHostToDevice, s));
+        EF_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
+    }
     if (off >= ((int64_t)1 << 32)) return EF_ERR_SIZE;
     if (q->cap_seg < q->nseg || q->cap_ctr < N + 3) {
         if (q->d_seg) cudaFree(q->d_seg);
@@ -328,6 +366,8 @@ int queue_set_meshes(Queue* q, const std::vector<ef_plan*>& plans, cudaStream_t 
         d.wseg = p->d_wseg;
         d.wpos_up = p->d_wpos_up;
         d.wpos_lo = p->d_wpos_lo;
+        d.wst_up = p->d_wst_up;
+        d.wst_lo = p->d_wst_lo;
         d.list = p->d_local;
         d.T = p->T;
         d.U = p->U;
@@ -367,6 +407,7 @@ int queue_init(Queue* q, int variant, int* shared_status)
     q->cfg.dynamic = 1;
     q->cfg.largest_first = 0;
     q->cfg.elem_ctas = 0;
+    q->cfg.two_launch = 0;
     q->cfg.ctas_per_sm = queue_max_ctas_per_sm(variant, 256);
     if (q->cfg.ctas_per_sm < 1) return EF_ERR_CUDA;
     return EF_OK;
@@ -374,9 +415,14 @@ int queue_init(Queue* q, int variant, int* shared_status)
 
 void queue_free(Queue* q)
 {
-    void* ptrs[] = {q->d_mesh, q->d_seg, q->d_need, q->d_ctrl, q->own_status ? q->d_status : nullptr};
+    void* ptrs[] = {q->d_mesh, q->d_seg, q->d_need, q->d_ctrl, q->own_status ? q->d_status : nullptr, q->d_eblk,
+                    q->d_sblk, q->d_emesh, q->d_smesh};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    q->d_eblk = q->d_sblk = nullptr;
+    q->d_emesh = q->d_smesh = nullptr;
+    q->cap_eblk = q->cap_sblk = 0;
+    q->nmesh = 0;
     q->d_mesh = nullptr;
     q->d_seg = nullptr;
     q->d_need = nullptr;
@@ -387,6 +433,9 @@ void queue_free(Queue* q)
 
 int queue_launch(const Queue* q, const QueueArgs& a, cudaStream_t s)
 {
+    if (q->cfg.two_launch && !a.nodes)
+        return launch_batch_two_pass(q->variant, q->d_mesh, q->d_emesh, q->d_eblk, q->n_eblk, q->d_smesh, q->d_sblk,
+                                     q->n_sblk, q->d_status, s);
     if (q->ntiles == 0) return EF_OK;
     return q->cfg.elems_per_tile == 128 ? launch_be<128>(q, a, s) : launch_be<256>(q, a, s);
 }

@@ -14,6 +14,8 @@ struct QueueMesh {              // device-side view of one mesh's plan
     const uint32_t* wseg;       // work item -> list range
     const uint32_t* wpos_up;    // work item -> CSR position of (r,c)
     const uint32_t* wpos_lo;    // work item -> CSR position of (c,r) or 0xffffffff
+    const void* wst_up;         // store orders of the sum kernel (ef_assemble.cu)
+    const void* wst_lo;
     double* list;               // 2 * np * T contribution values
     const double* nodes;        // bound buffers (batch); the single-mesh path passes them per call
     const double* coeff;
@@ -56,6 +58,15 @@ struct Queue {
     int64_t ntiles = 0;
     int64_t n_elem_tiles = 0;     // role split: tiles [0, n_elem_tiles) are element tiles
     int cap_mesh = 0, cap_seg = 0, cap_ctr = 0;
+    // two-launch schedule: first element block / first sum block of each
+    // mesh, and the mesh of every element block / sum block
+    int64_t* d_eblk = nullptr;
+    int64_t* d_sblk = nullptr;
+    uint32_t* d_emesh = nullptr;
+    uint32_t* d_smesh = nullptr;
+    int64_t n_eblk = 0, n_sblk = 0;
+    int64_t cap_eblk = 0, cap_sblk = 0;
+    int nmesh = 0;
 };
 
 int queue_init(Queue* q, int variant, int* shared_status);
@@ -65,5 +76,13 @@ int queue_build(Queue* q, const std::vector<ef_plan*>& plans, cudaStream_t s);
 int queue_launch(const Queue* q, const QueueArgs& a, cudaStream_t s);
 int queue_check(const Queue* q, cudaStream_t s);
 int queue_max_ctas_per_sm(int variant, int BE);
+
+// Batch in two launches (ef_assemble.cu): the element kernel over every
+// mesh's elements, then the sum kernel over every mesh's work items.
+int launch_batch_two_pass(int variant, const QueueMesh* d_mesh, const uint32_t* d_emesh, const int64_t* d_eblk,
+                          int64_t n_eblk, const uint32_t* d_smesh, const int64_t* d_sblk, int64_t n_sblk, int* status,
+                          cudaStream_t s);
+int64_t element_blocks(int64_t T);
+int64_t sum_blocks(int64_t U);
 
 }  // namespace ef

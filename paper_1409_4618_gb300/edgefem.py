@@ -56,7 +56,8 @@ class PlanInfo(C.Structure):
 
 class BatchConfig(C.Structure):
     _fields_ = [("elems_per_tile", C.c_int32), ("sum_tile", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("dynamic", C.c_int32), ("largest_first", C.c_int32), ("elem_ctas", C.c_int32)]
+                ("dynamic", C.c_int32), ("largest_first", C.c_int32), ("elem_ctas", C.c_int32),
+                ("two_launch", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,7 +1,7 @@
-"""Batched assembly (ef_batch_*) on the GPU: one persistent launch over many
-uneven meshes gives, mesh by mesh, exactly the bits of ef_assemble on that
-mesh (and so the oracle's values), under every schedule the autotuner can
-pick, and when replayed from a CUDA graph."""
+"""Batched assembly (ef_batch_*) on the GPU: one persistent launch (or the
+two-launch form) over many uneven meshes gives, mesh by mesh, exactly the bits
+of ef_assemble on that mesh (and so the oracle's values), under every schedule
+the autotuner can pick, and when replayed from a CUDA graph."""
 import numpy as np
 import pytest
 
@@ -83,14 +83,21 @@ def test_batch_every_schedule_and_the_tuner():
             for lf in (0, 1):
                 for st in (256, 4096):
                     batch.set_config(elems_per_tile=tile, dynamic=dyn, largest_first=lf, sum_tile=max(st, tile),
-                                     ctas_per_sm=2 if ec else 1, elem_ctas=ec)
+                                     ctas_per_sm=2 if ec else 1, elem_ctas=ec, two_launch=0)
                     for k in K + M:
                         k.fill_(float("nan"))
                     batch.assemble()
                     batch.assemble()          # queue counters reset themselves between launches
                     batch.check()
                     _same_bits(K, M, ref)
+    batch.set_config(two_launch=1)
+    for k in K + M:
+        k.fill_(float("nan"))
+    batch.assemble()
+    batch.check()
+    _same_bits(K, M, ref)
     cfg = batch.tune(reps=2)
+    assert cfg["two_launch"] in (0, 1)
     assert cfg["elems_per_tile"] in (128, 256) and cfg["ctas_per_sm"] >= 1
     for k in K + M:
         k.fill_(float("nan"))
