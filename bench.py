@@ -231,6 +231,60 @@ def run_batched(args, dev, plain_rate):
     return out
 
 
+def run_rt0(args, dev, peaks):
+    """The two RT0 workloads: 3D RT0 on the 128^3 cube (12,582,912 tets,
+    jitter 0.2h seed 3, log-uniform coefficient; the large, memory-heavy case)
+    and 2D RT0 on the 32^2 square (2,048 triangles, unit coefficient, no
+    jitter; launch-latency-bound). Same ef_assemble call, tuned, per-kernel
+    CUDA events, HBM fraction on the algorithmic bytes per call."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    out = {}
+    for name, dim, n, jitter, seed, unit in (("rt0_3d_kuhn128_jitter0.2", 3, 128, 0.2, 3, False),
+                                             ("rt0_2d_square32", 2, 32, 0.0, 0, True)):
+        if dim == 3:
+            nodes, elems = mg.kuhn_cube(n, jitter, seed)
+        else:
+            nodes, elems = mg.kuhn_square(n)
+        coeff = None if unit else mg.log_uniform_coeff(seed, elems.shape[0])
+        tn = torch.from_numpy(nodes).to(dev)
+        tc = None if coeff is None else torch.from_numpy(coeff).to(dev)
+        plan = ef.Plan(1, dim, nodes.shape[0], torch.from_numpy(elems).to(dev))
+        K = torch.empty(plan.nnz, dtype=torch.float64, device=dev)
+        M = torch.empty_like(K)
+        tuned = plan.tune(tn, tc, K, M, reps=3)
+        steps = args.rt0_steps if dim == 3 else 10 * args.rt0_steps
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            ef.ef_assemble(plan.handle, tn, tc, K, M, stream)
+        torch.cuda.synchronize()
+        plan.profile(steps)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            ef.ef_assemble(plan.handle, tn, tc, K, M, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        k1, k2, calls = plan.profile_read()
+        plan.profile(0)
+        plan.check()
+        T, V, nnz = elems.shape[0], nodes.shape[0], plan.nnz
+        alg = (4 * (dim + 1) + (0 if coeff is None else 8)) * T + 8 * dim * V + 16 * nnz
+        gbs = alg / (ms / 1e3) / 1e9
+        out[name] = {"value": T / (ms / 1e3) / 1e6, "unit": UNIT, "elements": int(T), "nnz": int(nnz),
+                     "ms_per_step": ms, "tuned_choice": tuned,
+                     "kernels_ms": {"first": k1 / max(calls, 1), "second": k2 / max(calls, 1)},
+                     "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                             "algorithmic_bytes_per_step": int(alg), "bytes_per_elem": alg / T}}
+        plan.close()
+        del K, M
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_adjoint(args, dev):
     """Adjoint of u^T K u + v^T M v on the 96^3 Nedelec workload (5,308,416
     tets, seed 5), against plain ef_assemble on the same mesh."""
@@ -447,6 +501,8 @@ def run_gpu(args):
         line["batched"] = run_batched(args, dev, value / ws)
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, dev)
+    if not args.no_rt0:
+        line["rt0"] = run_rt0(args, dev, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -466,6 +522,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-rt0", action="store_true")
+    ap.add_argument("--rt0-steps", type=int, default=20)
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--adjoint-steps", type=int, default=50)
