@@ -12,7 +12,9 @@ Prints one JSON line: throughput (M elements / s), e2e through the host-buffer
 C-ABI call, the roofline of the step's dominant kernel (timed per launch by
 CUDA events the library records on the launching stream inside the timed
 region), the HBM fraction of the whole step, the clocks seen while timing,
-and the CPU oracle timed on this host.
+the CPU oracle timed on this host, and the other workloads: batched (256
+meshes), adjoint (96^3), RT0 (3D 128^3, 2D 32^2) and the vectorised
+integration (L2 error at 27 points per element).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -285,6 +287,52 @@ def run_rt0(args, dev, peaks):
     return out
 
 
+def run_integration(args, dev, peaks):
+    """Vectorised integration (Sec. 3.1): squared L2 error ||E - v_h||^2 of an
+    affine field E against the Nedelec function of a random DOF vector on the
+    64^3 workload, 27-point rule (n = 3), E given at the points (point-major,
+    resident in HBM). Timed: ef_norm_l2 (per-element norms + fixed-order total)."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    w = WORKLOAD
+    nodes, elems, _ = _workload()
+    tn = torch.from_numpy(nodes).to(dev)
+    plan = ef.Plan(w["kind"], w["dim"], nodes.shape[0], torch.from_numpy(elems).to(dev))
+    n = 3
+    x = plan.quad_points(tn, n)
+    A = torch.from_numpy(mg.normal(7, 12, 9).reshape(3, 3)).to(dev)
+    f = (torch.einsum("qec,rc->qer", x, A) + 1.0).contiguous()
+    del x
+    v = torch.from_numpy(mg.normal(7, mg.STREAM_V, plan.n_dofs)).to(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        plan.norm_l2(tn, f, n, v=v, per_element=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = args.integration_steps
+    a.record(stream)
+    for _ in range(steps):
+        plan.norm_l2(tn, f, n, v=v, per_element=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    ms = a.elapsed_time(b) / steps
+    T, V = elems.shape[0], nodes.shape[0]
+    nq = n ** 3
+    alg = (nq * 3 * 8 + 16 + 24 + 1 + 8) * T + 24 * V + 8 * plan.n_dofs
+    gbs = alg / (ms / 1e3) / 1e9
+    out = {"value": T / (ms / 1e3) / 1e6, "unit": UNIT, "workload": w["name"] + "_l2error_q27",
+           "elements": int(T), "points_per_element": nq, "ms_per_step": ms,
+           "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                   "algorithmic_bytes_per_step": int(alg), "bytes_per_elem": alg / T}}
+    plan.close()
+    del f
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_adjoint(args, dev):
     """Adjoint of u^T K u + v^T M v on the 96^3 Nedelec workload (5,308,416
     tets, seed 5), against plain ef_assemble on the same mesh."""
@@ -503,6 +551,8 @@ def run_gpu(args):
         line["adjoint"] = run_adjoint(args, dev)
     if not args.no_rt0:
         line["rt0"] = run_rt0(args, dev, peaks)
+    if not args.no_integration:
+        line["integration"] = run_integration(args, dev, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -523,6 +573,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rt0", action="store_true")
+    ap.add_argument("--no-integration", action="store_true")
+    ap.add_argument("--integration-steps", type=int, default=50)
     ap.add_argument("--rt0-steps", type=int, default=20)
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)

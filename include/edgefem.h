@@ -254,6 +254,44 @@ void ef_plan_destroy(ef_plan* plan);
 int ef_adjoint(const ef_plan* plan, const double* d_nodes, const double* d_coeff, const double* d_u,
                const double* d_v, double* d_J, double* d_grad_nodes, double* d_grad_coeff, void* stream);
 
+/* ---- vectorised integration (Sec. 3.1, norm_L2) ------------------------------ */
+
+/* Quadrature: collapsed Gauss-Legendre product rule with n points per
+ * direction (1 <= n <= EF_QUAD_MAX_N): n^2 points on the triangle, n^3 on the
+ * tetrahedron, exact for polynomials of total degree 2n - dim. Triangle:
+ * xhat = (u, v(1-u)), weight w_u w_v (1-u); tetrahedron: xhat = (u, v(1-u),
+ * s(1-u)(1-v)), weight w_u w_v w_s (1-u)^2 (1-v), with (u, v, s) Gauss-Legendre
+ * nodes on [0, 1]; point q = (i n + j) n + k (3D), i n + j (2D). Weights sum
+ * to the reference measure (1/2, 1/6). */
+#define EF_QUAD_MAX_N 8
+
+/* The reference rule into host arrays h_xhat [nq x dim], h_w [nq] (cap
+ * entries; both may be NULL to query *nq). Host only, no GPU needed.
+ * Errors: EF_ERR_ARG (dim, n), EF_ERR_SIZE (cap < nq). */
+int ef_quad_rule(int dim, int n, double* h_xhat, double* h_w, int cap, int* nq);
+
+/* Physical quadrature points x = B_K xhat_q + P_K,0 of every element:
+ * d_x [nq][n_elems][dim] (point-major: for each point, all elements
+ * contiguous). Asynchronous. */
+int ef_quad_points(const ef_plan* plan, const double* d_nodes, int n, double* d_x, void* stream);
+
+/* Values at the same points of the finite-element function with DOF vector
+ * d_v [n_dofs]: v_h = sum_k s_k v[dof_k] phi_k, phi_k the Piola-mapped
+ * reference basis (RT0: B eta_k / det B = (x - P_opp(k)) / det B; Nedelec:
+ * B^-T eta_k, the Whitney form of edge k), s_k the orientation signs of
+ * ef_plan_topology. d_vals [nq][n_elems][dim]. Asynchronous. */
+int ef_fe_values(const ef_plan* plan, const double* d_nodes, const double* d_v, int n, double* d_vals,
+                 void* stream);
+
+/* Squared L2 norm of f - v_h (v_h omitted if d_v is NULL), f given by its
+ * values at the points of ef_quad_points: d_f [nq][n_elems][ncomp] (ncomp 1
+ * to 3; with d_v, ncomp = dim). Per element (d_elem [n_elems], may be NULL)
+ * |det B_K| sum_q w_q |f_q - v_h(x_q)|^2; total (d_total [1], may be NULL)
+ * summed in a fixed order. The first call allocates per-CTA scratch in the
+ * plan. Asynchronous. Errors: EF_ERR_ARG, EF_ERR_OOM. */
+int ef_norm_l2(ef_plan* plan, const double* d_nodes, int n, int ncomp, const double* d_f, const double* d_v,
+               double* d_elem, double* d_total, void* stream);
+
 /* ---- batched assembly of many meshes ---------------------------------------- */
 
 /*

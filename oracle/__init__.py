@@ -100,6 +100,8 @@ def _load():
                                      C.POINTER(_Result)]
         lib.ora_assemble2.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P, C.c_int, C.c_int,
                                       C.POINTER(_Result)]
+        lib.ora_quad_points.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P]
+        lib.ora_norm_l2.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, C.c_int, P, P, P, P]
         lib.ora_adjoint.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P, P, C.c_int, C.c_int,
                                     P, P, P]
         _lib = lib
@@ -191,6 +193,34 @@ def assemble2(kind: int, dim: int, nodes, elems, coeff_K=None, coeff_M=None, rul
         return _unpack(res, True)
     finally:
         lib.ora_free(C.byref(res))
+
+
+def quad_points(dim: int, nodes, elems, n: int):
+    """Physical points [nq, T, dim] of the collapsed Gauss-Legendre rule (n per direction)."""
+    lib = _load()
+    nodes, elems, _ = _prep(nodes, elems, None)
+    T = elems.shape[0]
+    nq = n ** dim
+    x = np.zeros((nq, T, dim))
+    m = lib.ora_quad_points(dim, nodes.shape[0], _ptr(nodes), T, _ptr(elems), n, _ptr(x))
+    if m < 0:
+        raise OracleError(m)
+    return x
+
+
+def norm_l2(kind: int, dim: int, nodes, elems, n: int, f, v=None):
+    """(total, per-element) squared L2 norm of f - v_h, f: [nq, T, ncomp] at quad_points."""
+    lib = _load()
+    nodes, elems, _ = _prep(nodes, elems, None)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    elem = np.zeros(elems.shape[0])
+    total = np.zeros(1)
+    st = lib.ora_norm_l2(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), n, f.shape[2],
+                         _ptr(f), _ptr(v), _ptr(elem), _ptr(total))
+    if st:
+        raise OracleError(st)
+    return float(total[0]), elem
 
 
 def local(kind: int, dim: int, P, sign, coeff: float = 1.0, rule: int = 0, n: int = 0):

@@ -26,7 +26,9 @@
  *     order into a CSR pattern holding every DOF pair that shares an element.
  * The adjoint (gradient of sum_K sigma_K (u_K^T Khat_K u_K + v_K^T Mhat_K v_K)
  * with respect to node coordinates and sigma) runs the same local-matrix code
- * on forward-mode dual numbers.
+ * on forward-mode dual numbers. The vectorised integration of Sec. 3.1
+ * (norm_L2: squared L2 norms by quadrature, loop over points, all elements
+ * at once) evaluates the same Piola-mapped, signed basis at quadrature points.
  */
 #include <math.h>
 #include <stdint.h>
@@ -865,6 +867,109 @@ int ora_adjoint(int kind, int dim, int64_t V, const double* nodes, int64_t T, co
         grad_coeff[e] = Je.d[12];
     }
     *J = Jsum;
+    ora_free(&topo);
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vectorised integration (Sec. 3.1, norm_L2)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Physical quadrature points x = B xhat_q + P_0 of every element for the
+ * collapsed Gauss-Legendre rule with n points per direction (rule 1),
+ * point-major: x[(q * T + e) * dim + c]. Returns the number of points. */
+int ora_quad_points(int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems, int n, double* x)
+{
+    static qrule q;
+    if ((dim != 2 && dim != 3) || V < 0 || T < 0) return ORA_ERR_ARG;
+    int st = make_rule(dim, 1, n, &q);
+    if (st) return st;
+    for (int64_t e = 0; e < T; e++) {
+        double P[4][3];
+        gather_points(dim, nodes, elems + e * (dim + 1), P);
+        for (int i = 0; i < q.n; i++)
+            for (int r = 0; r < dim; r++) {
+                double xr = P[0][r];
+                for (int c = 0; c < dim; c++) xr += (P[c + 1][r] - P[0][r]) * q.x[3 * i + c];
+                x[((int64_t)i * T + e) * dim + r] = xr;
+            }
+    }
+    return q.n;
+}
+
+/* Squared L2 norm, element by element, of f - v_h over the mesh by the same
+ * rule: elem_out[e] = |det B_K| sum_q w_q |f_q - v_h(x_q)|^2 (the paper's
+ * fnorm), *total = their sum in element order. f: [q][element][ncomp] at the
+ * points of ora_quad_points; v: DOF vector (n_dofs) or NULL (v_h = 0), with
+ * v_h = sum_k s_k v[dof_k] phi_k, phi_k = (1/det B) B eta_k (RT0, Eq.
+ * RT0piola) or B^-T eta_k (Nedelec, Ned0piola1) at xhat_q, s_k the geometric
+ * signs. elem_out may be NULL. */
+int ora_norm_l2(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems, int n, int ncomp,
+                const double* f, const double* v, double* elem_out, double* total)
+{
+    static qrule q;
+    ora_result topo;
+    memset(&topo, 0, sizeof(topo));
+    if (!valid_kind(kind, dim) || ncomp < 1 || ncomp > 3 || (v && ncomp != dim)) return ORA_ERR_ARG;
+    int st = make_rule(dim, 1, n, &q);
+    if (st) return st;
+    if (v) {
+        st = ora_topology(kind, dim, V, nodes, T, elems, &topo);
+        if (st) return st;
+    }
+    const affine_field* basis = ref_basis(kind, dim);
+    int nl = nloc_of(kind, dim);
+    double sum = 0.0;
+    for (int64_t e = 0; e < T; e++) {
+        double P[4][3], B[3][3], Bi[3][3];
+        gather_points(dim, nodes, elems + e * (dim + 1), P);
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) B[r][c] = (r < dim && c < dim) ? P[c + 1][r] - P[0][r] : (r == c ? 1.0 : 0.0);
+        double det = det_of(dim, P);
+        if (det == 0.0) {
+            ora_free(&topo);
+            return ORA_ERR_DEGENERATE;
+        }
+        /* B^-1 = adj(B) / det (cofactors; the 2D case has B[2][2] = 1) */
+        Bi[0][0] = (B[1][1] * B[2][2] - B[1][2] * B[2][1]) / det;
+        Bi[0][1] = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) / det;
+        Bi[0][2] = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) / det;
+        Bi[1][0] = (B[1][2] * B[2][0] - B[1][0] * B[2][2]) / det;
+        Bi[1][1] = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) / det;
+        Bi[1][2] = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) / det;
+        Bi[2][0] = (B[1][0] * B[2][1] - B[1][1] * B[2][0]) / det;
+        Bi[2][1] = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) / det;
+        Bi[2][2] = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) / det;
+        double acc = 0.0;
+        for (int i = 0; i < q.n; i++) {
+            const double* xh = q.x + 3 * i;
+            double vh[3] = {0.0, 0.0, 0.0};
+            if (v) {
+                for (int k = 0; k < nl; k++) {
+                    double eta[3] = {0.0, 0.0, 0.0}, phi[3] = {0.0, 0.0, 0.0};
+                    for (int r = 0; r < dim; r++) {
+                        eta[r] = basis[k].a[r];
+                        for (int c = 0; c < dim; c++) eta[r] += basis[k].A[r][c] * xh[c];
+                    }
+                    for (int r = 0; r < dim; r++)
+                        for (int c = 0; c < dim; c++)
+                            phi[r] += (kind == ORA_RT0) ? B[r][c] * eta[c] / det : Bi[c][r] * eta[c];
+                    double coef = topo.sign[e * nl + k] * v[topo.elem2dof[e * nl + k]];
+                    for (int r = 0; r < dim; r++) vh[r] += coef * phi[r];
+                }
+            }
+            double d2 = 0.0;
+            for (int c = 0; c < ncomp; c++) {
+                double d = f[((int64_t)i * T + e) * ncomp + c] - vh[c];
+                d2 += d * d;
+            }
+            acc += q.w[i] * d2;
+        }
+        double ne = fabs(det) * acc;
+        if (elem_out) elem_out[e] = ne;
+        sum += ne;
+    }
+    if (total) *total = sum;
     ora_free(&topo);
     return ORA_OK;
 }

@@ -141,6 +141,9 @@ struct ef_plan {
 
     // per-kernel CUDA events of ef_assemble calls (ef_plan_profile)
     struct ef::Profile* prof;
+
+    // per-CTA partial norms of ef_norm_l2 (allocated on first use)
+    double* d_l2_part;
 };
 
 namespace ef {

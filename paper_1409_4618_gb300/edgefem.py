@@ -116,6 +116,10 @@ def load():
             "ef_batch_set_config": ([P, C.POINTER(BatchConfig), P], I),
             "ef_batch_check": ([P, P], I),
             "ef_batch_destroy": ([P], None),
+            "ef_quad_rule": ([I, I, P, P, I, C.POINTER(C.c_int)], I),
+            "ef_quad_points": ([P, P, I, P, P], I),
+            "ef_fe_values": ([P, P, P, I, P, P], I),
+            "ef_norm_l2": ([P, P, I, I, P, P, P, P, P], I),
             "ef_status_string": ([I], C.c_char_p),
             "ef_last_error": ([], C.c_char_p),
         }
@@ -367,6 +371,35 @@ class Plan:
         ef_assemble_host(self.handle, nodes, coeff, K, M, stream)
         return K, M
 
+    def quad_points(self, nodes, n: int, stream=None):
+        """Physical quadrature points [nq, n_elems, dim] (point-major)."""
+        nq = n ** self.dim
+        x = torch.empty((nq, self.n_elems, self.dim), dtype=torch.float64, device=self.device)
+        _check(load().ef_quad_points(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
+                                     C.c_void_p(x.data_ptr()), _stream_ptr(stream)))
+        return x
+
+    def fe_values(self, nodes, v, n: int, stream=None):
+        """Values [nq, n_elems, dim] of the FE function with DOF vector v at the quadrature points."""
+        nq = n ** self.dim
+        out = torch.empty((nq, self.n_elems, self.dim), dtype=torch.float64, device=self.device)
+        _check(load().ef_fe_values(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(v, torch.float64, "v"),
+                                   int(n), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def norm_l2(self, nodes, f, n: int, v=None, per_element: bool = False, stream=None):
+        """Squared L2 norm of f (values [nq, n_elems, ncomp] at the quadrature points), minus the FE
+        function of v if given: (total [1], per-element [n_elems] or None)."""
+        if not f.is_contiguous() or f.dim() != 3:
+            raise TypeError("f must be a contiguous [nq, n_elems, ncomp] tensor")
+        total = torch.empty(1, dtype=torch.float64, device=self.device)
+        elem = torch.empty(self.n_elems, dtype=torch.float64, device=self.device) if per_element else None
+        _check(load().ef_norm_l2(self.handle, _dev(nodes, torch.float64, "nodes"), int(n), int(f.shape[2]),
+                                 _dev(f, torch.float64, "f"), _dev(v, torch.float64, "v"),
+                                 _dev(elem, torch.float64, "elem"), C.c_void_p(total.data_ptr()),
+                                 _stream_ptr(stream)))
+        return total, elem
+
     def adjoint(self, nodes, coeff, u, v, stream=None):
         """(J, dJ/dnodes, dJ/dcoeff) of J = u^T K u + v^T M v (3D Nedelec)."""
         J = torch.empty(1, dtype=torch.float64, device=self.device)
@@ -400,6 +433,18 @@ def _ptr_array(tensors, dtype, name, allow_none=False):
         else:
             out[i] = _dev(t, dtype, f"{name}[{i}]")
     return out
+
+
+def ef_quad_rule(dim: int, n: int):
+    """Reference points [nq, dim] and weights [nq] of the library's rule (host)."""
+    import numpy as np
+
+    nq = C.c_int()
+    _check(load().ef_quad_rule(dim, n, None, None, 0, C.byref(nq)))
+    x = np.zeros((nq.value, dim))
+    w = np.zeros(nq.value)
+    _check(load().ef_quad_rule(dim, n, C.c_void_p(x.ctypes.data), C.c_void_p(w.ctypes.data), nq.value, C.byref(nq)))
+    return x, w
 
 
 class _Energy(torch.autograd.Function):

@@ -1,0 +1,111 @@
+"""Pins of the vectorised integration (Sec. 3.1, norm_L2) (no GPU).
+
+* The library's reference rule (ef_quad_rule, host code) integrates every
+  monomial x^a y^b (z^c) of total degree <= 2n - dim exactly: the closed form
+  over the reference simplex is a! b! c! / (a + b + c + dim)!.
+* The oracle's norm: |Omega| for f = 1; closed-form integrals of polynomial
+  fields over the unit square / cube; ||v_h||^2 = v^T M v with the oracle's
+  pinned mass matrix (unit coefficient); the interpolant of a constant field
+  c reproduces c at every quadrature point, so ||c - v_h||^2 vanishes and
+  ||v_h||^2 = |Omega| |c|^2. A wrong Piola map, sign, weight or Jacobian
+  fails one of these.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1409_4618_gb300 import meshgen as mg
+from tests._bruteforce import to_dense
+
+RT0, NED1 = 1, 2
+CASES = [(RT0, 2), (NED1, 2), (RT0, 3), (NED1, 3)]
+
+
+def _mesh(dim, n, seed):
+    if dim == 3:
+        nodes, elems = mg.kuhn_cube(n, 0.2, seed)
+    else:
+        nodes, elems = mg.kuhn_square(n, 0.2, seed)
+    return nodes, mg.shuffle_local_order(elems, seed + 100)
+
+
+def _constant_dofs(kind, dim, nodes, d2n, c):
+    Xa, Xb = nodes[d2n[:, 0]], nodes[d2n[:, 1]]
+    if kind == NED1:
+        return (Xa - Xb) @ c
+    if dim == 2:
+        t = Xa - Xb
+        return np.stack([t[:, 1], -t[:, 0]], 1) @ c
+    return np.cross(Xb - Xa, nodes[d2n[:, 2]] - Xa) @ c
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_library_rule_exactness(dim):
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    for n in range(1 if dim == 2 else 2, 9):
+        x, w = ef.ef_quad_rule(dim, n)
+        assert x.shape == (n ** dim, dim) and np.all(w > 0)
+        deg = 2 * n - dim
+        for a in range(deg + 1):
+            for b in range(deg + 1 - a):
+                for c in (range(deg + 1 - a - b) if dim == 3 else [0]):
+                    exact = math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + dim)
+                    mono = x[:, 0] ** a * x[:, 1] ** b * (x[:, 2] ** c if dim == 3 else 1.0)
+                    assert abs(w @ mono - exact) <= 1e-14 * exact, (n, a, b, c)
+        # points inside the reference simplex
+        assert np.all(x >= 0) and np.all(x.sum(1) <= 1 + 1e-15)
+
+
+def test_library_rule_rejects_bad_arguments():
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    for dim, n in ((3, 0), (2, 9), (4, 2)):
+        with pytest.raises(ef.EdgeFemError):
+            ef.ef_quad_rule(dim, n)
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_oracle_norm_of_polynomials(ora, kind, dim):
+    nodes, elems = _mesh(dim, 3, 31)
+    n = 4
+    x = ora.quad_points(dim, nodes, elems, n)
+    one = np.ones(x.shape[:2] + (1,))
+    assert abs(ora.norm_l2(kind, dim, nodes, elems, n, one)[0] - 1.0) < 1e-14
+    if dim == 3:
+        f = (x[..., 0] * x[..., 1] + x[..., 2])[..., None]
+        exact = 1.0 / 9 + 1.0 / 4 + 1.0 / 3
+    else:
+        f = (x[..., 0] * x[..., 1] + 1.0)[..., None]
+        exact = 1.0 / 9 + 1.0 / 2 + 1.0
+    total, elem = ora.norm_l2(kind, dim, nodes, elems, n, f)
+    assert abs(total - exact) < 1e-13 * exact
+    assert abs(elem.sum() - total) < 1e-14 * total
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_oracle_norm_of_fe_function_is_mass_energy(ora, kind, dim):
+    nodes, elems = _mesh(dim, 3, 33)
+    r = ora.assemble(kind, dim, nodes, elems)
+    M = to_dense(r, "M")
+    v = mg.normal(33, mg.STREAM_V, r["n_dofs"])
+    n = 3
+    zero = np.zeros((n ** dim, elems.shape[0], dim))
+    total, _ = ora.norm_l2(kind, dim, nodes, elems, n, zero, v)
+    assert abs(total - v @ M @ v) < 1e-13 * (v @ M @ v)
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_oracle_interpolant_of_constant_is_exact(ora, kind, dim):
+    nodes, elems = _mesh(dim, 3, 35)
+    r = ora.topology(kind, dim, nodes, elems)
+    c = np.array([0.7, -1.3, 0.4])[:dim]
+    u = _constant_dofs(kind, dim, nodes, r["dof2nodes"], c)
+    n = 2
+    cf = np.broadcast_to(c, (n ** dim, elems.shape[0], dim)).copy()
+    err, _ = ora.norm_l2(kind, dim, nodes, elems, n, cf, u)
+    assert err < 1e-26
+    zero = np.zeros_like(cf)
+    energy, _ = ora.norm_l2(kind, dim, nodes, elems, n, zero, u)
+    assert abs(energy - c @ c) < 1e-13
