@@ -92,6 +92,21 @@ def _dist():
     return ws, rank
 
 
+def job_timing(ms_local: float, units_local: float, dist=None, device="cpu"):
+    """Whole-job timing over the ranks: (max of the ranks' milliseconds, sum of
+    the units they processed). Without a process group, the local values."""
+    import torch
+
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+    if dist is None:
+        return float(t[0]), float(t[1])
+    ms = t[:1].clone()
+    units = t[1:].clone()
+    dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    return float(ms.item()), float(units.item())
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -460,12 +475,9 @@ def run_gpu(args):
     plan.check()
     k_first, k_second, k_calls = plan.profile_read() if path != "two_pass" else (0.0, 0.0, 0)
     plan.profile(0)
-    ms_t = torch.tensor([ms], device=dev)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms, units = job_timing(ms, T * args.steps, dist, dev)
     ms_step = ms / args.steps
-    value = ws * T * args.steps / (ms / 1e3) / 1e6
+    value = units / (ms / 1e3) / 1e6
 
     # ---- end to end through the host-buffer C-ABI call
     hn = torch.from_numpy(nodes).pin_memory()
@@ -485,11 +497,8 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
-    e2e_t = torch.tensor([statistics.median(e2e_times)], device=dev)
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
-    e2e = {"value": ws * T / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
+    e2e_ms, e2e_units = job_timing(statistics.median(e2e_times), T, dist, dev)
+    e2e = {"value": e2e_units / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
            "steps": e2e_steps, "timing": "median of per-step CUDA events around ef_assemble_host",
            "h2d_bytes_per_step": int(hn.numel() * 8 + hc.numel() * 8),
            "d2h_bytes_per_step": int(2 * nnz * 8)}
@@ -503,7 +512,7 @@ def run_gpu(args):
     n_pairs = info["n_contrib"] // T
     elem_ops = T * fp64_ops_per_element(w["kind"], w["dim"])
     sum_ops = 2 * (T * n_pairs - U)
-    sum_bytes = 2 * n_pairs * 8 * T + 12 * U + 16 * nnz
+    sum_bytes = 2 * n_pairs * 8 * T + 14 * U + 16 * nnz   # list, indices + store orders, CSR values
     if k_calls > 0 and info["fused_block"] == 0 and info["assemble_launches"] == 2:
         ms_e, ms_s = k_first / k_calls, k_second / k_calls
         kernels = {"element": {"ms_per_launch": ms_e, "share": ms_e / (ms_e + ms_s)},
