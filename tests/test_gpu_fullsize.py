@@ -1,10 +1,13 @@
-"""GPU parity on the full-size workloads, against the full oracle (needs a GB300).
+"""GPU parity on the full-size workloads (needs a GB300).
 
 3D Nedelec 64^3 (1,572,864 tets), 3D RT0 128^3 (12,582,912 tets) and 3D
 Nedelec 96^3 (5,308,416 tets), jittered +-0.2h, coefficient log-uniform in
 [0.1, 10]: topology and CSR pattern bit for bit, K and M within 1e-12 of
 max(|oracle|, sum |contributions|), through the same ef_assemble launch the
-benchmark times. Oracle time on one core is about 12 s, 80 s and 50 s.
+benchmark times, against the full oracle (about 12 s, 80 s and 50 s on one
+core). The benchmark's batch (256 meshes): sampled meshes against the
+oracle. The benchmark's adjoint (96^3): size-independent identities and
+sampled per-element coefficient gradients against the oracle.
 """
 import gc
 
@@ -30,3 +33,86 @@ def test_fullsize_parity(ora, name, kind, n, seed):
     print(name, stats)
     del g, o
     gc.collect()
+
+
+def test_fullsize_batch_sampled_meshes(ora):
+    """The benchmark's batch (256 cubes, n ~ U{8..48}, seed 4; mesh b jittered
+    with seed 4000 + b) under the tuned schedule: the first, last, smallest and
+    largest meshes against the oracle."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+    from tests._parity import entry_scale
+
+    sizes = mg.batch_sizes(4, 256, 8, 48)
+    meshes = [mg.kuhn_cube(int(n), 0.2, 4000 + b) for b, n in enumerate(sizes)]
+    coeffs = [mg.log_uniform_coeff(4000 + b, el.shape[0]) for b, (_, el) in enumerate(meshes)]
+    dev = torch.device("cuda")
+    batch = ef.Batch(NED1, 3, [nd.shape[0] for nd, _ in meshes], [torch.from_numpy(el).to(dev) for _, el in meshes])
+    K = [torch.empty(z, dtype=torch.float64, device=dev) for z in batch.nnz]
+    M = [torch.empty_like(k) for k in K]
+    batch.bind([torch.from_numpy(nd).to(dev) for nd, _ in meshes], [torch.from_numpy(c).to(dev) for c in coeffs],
+               K, M)
+    batch.tune(reps=2)
+    for k in K + M:
+        k.fill_(float("nan"))
+    batch.assemble()
+    batch.check()
+    for i in sorted({0, 255, int(np.argmin(sizes)), int(np.argmax(sizes))}):
+        nodes, elems = meshes[i]
+        o = ora.assemble(NED1, 3, nodes, elems, coeffs[i])
+        rowptr, colidx = batch.pattern(i)
+        np.testing.assert_array_equal(rowptr.cpu().numpy(), o["rowptr"])
+        np.testing.assert_array_equal(colidx.cpu().numpy(), o["colidx"])
+        for key, g in (("K", K[i]), ("M", M[i])):
+            assert np.all(np.abs(g.cpu().numpy() - o[key]) <= 1e-12 * entry_scale(o, key)), (i, key)
+    batch.close()
+
+
+def test_fullsize_adjoint_properties_and_sampled_coefficient_gradient(ora):
+    """The benchmark's adjoint workload (96^3, seed 5): identities that hold at
+    any size -- sum_e sigma_e dJ/dsigma_e = J, zero net force and torque
+    (translation and rotation invariance), sum_i x_i . dJ/dx_i = u^T K u (-1)
+    + v^T M v (K scales like 1/length, M like length) -- and dJ/dsigma_e =
+    u_e^T Khat_e u_e + v_e^T Mhat_e v_e against the oracle's local matrices on
+    sampled elements."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(96, 0.2, 5)
+    coeff = mg.log_uniform_coeff(5, elems.shape[0])
+    dev = torch.device("cuda")
+    plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).to(dev))
+    u = mg.normal(5, mg.STREAM_U, plan.n_dofs)
+    v = mg.normal(5, mg.STREAM_V, plan.n_dofs)
+    tn, tc = torch.from_numpy(nodes).to(dev), torch.from_numpy(coeff).to(dev)
+    tu, tv = torch.from_numpy(u).to(dev), torch.from_numpy(v).to(dev)
+    J, gx, gs = plan.adjoint(tn, tc, tu, tv)
+    K, M = plan.assemble(tn, tc)
+    plan.check()
+    rowptr, colidx = plan.pattern()
+    rows = torch.repeat_interleave(torch.arange(plan.n_dofs, device=dev), torch.diff(rowptr))
+    JK = float((tu[rows] * K * tu[colidx.long()]).sum())
+    JM = float((tv[rows] * M * tv[colidx.long()]).sum())
+    J = float(J[0])
+    assert abs(J - (JK + JM)) <= 1e-10 * abs(J)
+    assert abs(float((tc * gs).sum()) - J) <= 1e-10 * abs(J)
+    gxn = gx.cpu().numpy()
+    scale = np.abs(gxn).sum(0)
+    assert np.all(np.abs(gxn.sum(0)) <= 1e-10 * scale)
+    torque = np.cross(nodes, gxn).sum(0)
+    assert np.all(np.abs(torque) <= 1e-10 * (np.abs(nodes).max() * scale.sum()))
+    euler = float((nodes * gxn).sum())
+    assert abs(euler - (JM - JK)) <= 1e-9 * (abs(JK) + abs(JM))
+    # sampled elements: dJ/dsigma_e from the oracle's local matrices and signs
+    topo = ora.topology(NED1, 3, nodes, elems)
+    gsn = gs.cpu().numpy()
+    T = elems.shape[0]
+    for e in (0, 1, T // 3, T // 2 + 7, T - 1):
+        P = nodes[elems[e]]
+        Kl, Ml = ora.local(NED1, 3, P, topo["sign"][e].astype(np.float64), 1.0)
+        d = topo["elem2dof"][e]
+        expect = u[d] @ Kl @ u[d] + v[d] @ Ml @ v[d]
+        assert abs(gsn[e] - expect) <= 1e-11 * (abs(u[d]) @ np.abs(Kl) @ abs(u[d]) + abs(v[d]) @ np.abs(Ml) @ abs(v[d]))
+    plan.close()
