@@ -34,6 +34,7 @@ namespace ef {
 namespace {
 
 constexpr int TPB = 256;
+constexpr int EPB = 128;   // threads (elements) per CTA of the element kernels: 6 CTAs of 80 registers per SM
 
 // Writes each contribution to its slot in the nonzero-ordered contribution
 // list: inv[q * T + e] = position of (element e, pair q). K values occupy
@@ -59,14 +60,14 @@ __device__ __forceinline__ void element_body(const int32_t* __restrict__ elems, 
 }
 
 template <int VAR>
-__global__ void __launch_bounds__(TPB, 3) k_element_local(const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(EPB, 6) k_element_local(const int32_t* __restrict__ elems,
                                                        const double* __restrict__ nodes,
                                                        const double* __restrict__ coeffK,
                                                        const double* __restrict__ coeffM,
                                                        const uint32_t* __restrict__ inv, int64_t e0, int64_t e1,
                                                        int64_t T, double* __restrict__ list, int* status)
 {
-    const int64_t e = e0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const int64_t e = e0 + (int64_t)blockIdx.x * EPB + threadIdx.x;
     if (e >= e1) return;
     element_body<VAR>(elems, nodes, coeffK, coeffM, inv, e, T, list, status);
 }
@@ -91,13 +92,13 @@ __device__ __forceinline__ int64_t load_block_mesh(const QueueMesh* __restrict__
 // The element kernel over every mesh of a batch: CTA b takes TPB elements of
 // mesh m, blocks of meshes one after the other (blk_off: prefix of blocks).
 template <int VAR>
-__global__ void __launch_bounds__(TPB, 3) k_batch_element(const QueueMesh* __restrict__ md,
+__global__ void __launch_bounds__(EPB, 6) k_batch_element(const QueueMesh* __restrict__ md,
                                                        const uint32_t* __restrict__ blk_mesh,
                                                        const int64_t* __restrict__ blk_off, int* status)
 {
     __shared__ QueueMesh d;
     __shared__ int64_t first;
-    const int64_t e = load_block_mesh(md, blk_mesh, blk_off, d, &first) * TPB + threadIdx.x;
+    const int64_t e = load_block_mesh(md, blk_mesh, blk_off, d, &first) * EPB + threadIdx.x;
     if (e >= d.T) return;
     element_body<VAR>(d.elems, d.nodes, d.coeff, d.coeff, d.inv, e, d.T, d.list, status);
 }
@@ -287,12 +288,12 @@ int element_range(const ef_plan* p, const double* nodes, const double* cK, const
                   cudaStream_t s)
 {
     if (e1 <= e0) return EF_OK;
-    const unsigned grid = (unsigned)((e1 - e0 + TPB - 1) / TPB);
+    const unsigned grid = (unsigned)((e1 - e0 + EPB - 1) / EPB);
     switch (p->variant) {
-        case RT2: k_element_local<RT2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        case NED2: k_element_local<NED2><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        case RT3: k_element_local<RT3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        default: k_element_local<NED3><<<grid, TPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT2: k_element_local<RT2><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case NED2: k_element_local<NED2><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT3: k_element_local<RT3><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        default: k_element_local<NED3><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
     }
     EF_CUDA(cudaGetLastError());
     return EF_OK;
@@ -451,10 +452,10 @@ int launch_batch_two_pass(int variant, const QueueMesh* d_mesh, const uint32_t* 
     if (n_eblk > 0) {
         const unsigned g = (unsigned)n_eblk;
         switch (variant) {
-            case RT2: k_batch_element<RT2><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
-            case NED2: k_batch_element<NED2><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
-            case RT3: k_batch_element<RT3><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
-            default: k_batch_element<NED3><<<g, TPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+            case RT2: k_batch_element<RT2><<<g, EPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+            case NED2: k_batch_element<NED2><<<g, EPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+            case RT3: k_batch_element<RT3><<<g, EPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
+            default: k_batch_element<NED3><<<g, EPB, 0, s>>>(d_mesh, d_emesh, d_eblk, status); break;
         }
     }
     if (n_sblk > 0) {
@@ -470,7 +471,7 @@ int launch_batch_two_pass(int variant, const QueueMesh* d_mesh, const uint32_t* 
     return EF_OK;
 }
 
-int64_t element_blocks(int64_t T) { return (T + TPB - 1) / TPB; }
+int64_t element_blocks(int64_t T) { return (T + EPB - 1) / EPB; }
 int64_t sum_blocks(int64_t U) { return (U + SB - 1) / SB; }
 
 int launch_two_pass_chunk(const ef_plan* p, int c, const double* nodes, const double* coeff, double* K, double* M,
