@@ -124,7 +124,8 @@ int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream);
  * element chunks, 128 or 256 elements per tile, 1024 or 4096 nonzeros per
  * sum tile and 0, 1 or 2 element-only CTAs per four (*chosen = chunks*100 +
  * elem_ctas*10 + (tile == 256)); the element-block path (*chosen = -block).
- * Overwrites d_Kval / d_Mval. Synchronises `stream`. */
+ * A candidate whose schedule cannot be built (EF_ERR_OOM, EF_ERR_SIZE) is
+ * skipped. Overwrites d_Kval / d_Mval. Synchronises `stream`. */
 int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
                  int reps, int* chosen, void* stream);
 

@@ -326,6 +326,11 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
             plan->use_two_pass = 0;
             if (st == EF_OK) st = plan_queue_config(plan, c.q, s);
         }
+        if (st == EF_ERR_OOM || st == EF_ERR_SIZE) {   // a schedule that does not fit: skip it
+            cudaGetLastError();
+            st = EF_OK;
+            continue;
+        }
         if (st != EF_OK) break;
         if ((st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream)) != EF_OK) break;
         cudaEventRecord(e0, s);
