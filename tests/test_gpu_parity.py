@@ -303,3 +303,28 @@ def test_cuda_graph_capture_replays_bitwise():
     assert torch.equal(K.view(torch.int64), K1.view(torch.int64))
     plan.check()
     plan.close()
+
+
+@pytest.mark.parametrize("kind", [RT0, NED1])
+def test_fig3_shared_edge_signs_gpu(kind):
+    """The paper's Fig. 3 orientation example through the C ABI: sign bit of
+    K_n's shared edge clear (+1), of K_m's set (-1), same global edge."""
+    import json
+    import os
+
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fig3_shared_edge_signs.json")) as f:
+        g = json.load(f)
+    elems = np.array([g["elems"]["K_n"], g["elems"]["K_m"]], dtype=np.int32)
+    plan = ef.Plan(kind, 2, len(g["nodes"]), torch.from_numpy(elems).cuda())
+    e2d, sb, _ = plan.topology()
+    e2d, sb = e2d.cpu().numpy(), sb.cpu().numpy()
+    ex = g["expected"]
+    kn, km = ex["K_n_shared_local_edge"], ex["K_m_shared_local_edge"]
+    assert ((sb[0] >> kn) & 1) == (0 if ex["K_n_sign"] > 0 else 1)
+    assert ((sb[1] >> km) & 1) == (0 if ex["K_m_sign"] > 0 else 1)
+    assert e2d[0][kn] == e2d[1][km]
+    plan.close()

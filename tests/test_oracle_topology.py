@@ -171,3 +171,23 @@ def test_error_codes(ora):
     with pytest.raises(ora.OracleError) as e:
         ora.assemble(RT0, 3, flat, elems)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_fig3_shared_edge_signs(ora, kind):
+    """The paper's worked orientation example (Fig. 3): with node c > node a the
+    shared edge gets +1 in K_n and the opposite sign in K_m, for RT0 (normal)
+    and Nedelec (tangential) alike, and both elements point to the same
+    global edge."""
+    with open(os.path.join(GOLD, "fig3_shared_edge_signs.json")) as f:
+        g = json.load(f)
+    nodes = np.array(g["nodes"])
+    elems = np.array([g["elems"]["K_n"], g["elems"]["K_m"]], dtype=np.int32)
+    r = ora.topology(kind, 2, nodes, elems)
+    ex = g["expected"]
+    kn, km = ex["K_n_shared_local_edge"], ex["K_m_shared_local_edge"]
+    assert r["sign"][0][kn] == ex["K_n_sign"]
+    assert r["sign"][1][km] == ex["K_m_sign"]
+    assert r["elem2dof"][0][kn] == r["elem2dof"][1][km]
+    a, c = g["node_names"]["a"], g["node_names"]["c"]
+    assert sorted(r["dof2nodes"][r["elem2dof"][0][kn]].tolist()) == sorted([a, c])
