@@ -293,6 +293,19 @@ int ef_fe_values(const ef_plan* plan, const double* d_nodes, const double* d_v, 
 int ef_norm_l2(ef_plan* plan, const double* d_nodes, int n, int ncomp, const double* d_f, const double* d_v,
                double* d_elem, double* d_total, void* stream);
 
+/* Per-element curl (Nedelec) or divergence (RT0) of the FE function with DOF
+ * vector d_v, constant on each element: d_out [n_elems] (2D Nedelec, RT0) or
+ * [n_elems x 3] (3D Nedelec). Asynchronous. */
+int ef_fe_curl(const ef_plan* plan, const double* d_nodes, const double* d_v, double* d_out, void* stream);
+
+/* Load vector b_i = int_Omega F . eta_i by the rule with n points per
+ * direction, F given at the points of ef_quad_points: d_F [nq][n_elems][dim];
+ * d_b [n_dofs]. Each b_i is the sum of its elements' contributions in
+ * ascending element order (bitwise reproducible). The first call builds a
+ * DOF-to-element incidence and scratch in the plan (allocates,
+ * synchronises `stream`). Asynchronous afterwards. */
+int ef_load_vector(ef_plan* plan, const double* d_nodes, int n, const double* d_F, double* d_b, void* stream);
+
 /* ---- batched assembly of many meshes ---------------------------------------- */
 
 /*

@@ -102,6 +102,9 @@ def _load():
                                       C.POINTER(_Result)]
         lib.ora_quad_points.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P]
         lib.ora_norm_l2.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, C.c_int, P, P, P, P]
+        lib.ora_load_vector.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P, P]
+        lib.ora_fe_values.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P, P]
+        lib.ora_fe_curl.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P]
         lib.ora_adjoint.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P, P, C.c_int, C.c_int,
                                     P, P, P]
         _lib = lib
@@ -221,6 +224,43 @@ def norm_l2(kind: int, dim: int, nodes, elems, n: int, f, v=None):
     if st:
         raise OracleError(st)
     return float(total[0]), elem
+
+
+def load_vector(kind: int, dim: int, nodes, elems, n: int, F):
+    """b_i = int F . eta_i, F: [nq, T, dim] at quad_points (n per direction)."""
+    lib = _load()
+    nodes, elems, _ = _prep(nodes, elems, None)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    N = topology(kind, dim, nodes, elems)["n_dofs"]
+    b = np.zeros(N)
+    st = lib.ora_load_vector(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), n, _ptr(F), _ptr(b))
+    if st:
+        raise OracleError(st)
+    return b
+
+
+def fe_values(kind: int, dim: int, nodes, elems, n: int, v):
+    """Values [nq, T, dim] of v_h at quad_points."""
+    lib = _load()
+    nodes, elems, _ = _prep(nodes, elems, None)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros((n ** dim, elems.shape[0], dim))
+    st = lib.ora_fe_values(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), n, _ptr(v), _ptr(out))
+    if st:
+        raise OracleError(st)
+    return out
+
+
+def fe_curl(kind: int, dim: int, nodes, elems, v):
+    """Per-element curl (Nedelec) or divergence (RT0) of v_h: [T] or [T, 3] (3D Nedelec)."""
+    lib = _load()
+    nodes, elems, _ = _prep(nodes, elems, None)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros((elems.shape[0], 3) if (kind == NED1 and dim == 3) else elems.shape[0])
+    st = lib.ora_fe_curl(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), _ptr(v), _ptr(out))
+    if st:
+        raise OracleError(st)
+    return out
 
 
 def local(kind: int, dim: int, P, sign, coeff: float = 1.0, rule: int = 0, n: int = 0):

@@ -973,3 +973,158 @@ int ora_norm_l2(int kind, int dim, int64_t V, const double* nodes, int64_t T, co
     ora_free(&topo);
     return ORA_OK;
 }
+
+/* Shared by the functions below: B (dim x dim, identity-padded), B^-1, det. */
+static int element_frame(int dim, const double* nodes, const int32_t* el, double P[4][3], double B[3][3],
+                         double Bi[3][3], double* det)
+{
+    gather_points(dim, nodes, el, P);
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) B[r][c] = (r < dim && c < dim) ? P[c + 1][r] - P[0][r] : (r == c ? 1.0 : 0.0);
+    *det = det_of(dim, P);
+    if (*det == 0.0) return ORA_ERR_DEGENERATE;
+    double d = *det;
+    Bi[0][0] = (B[1][1] * B[2][2] - B[1][2] * B[2][1]) / d;
+    Bi[0][1] = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) / d;
+    Bi[0][2] = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) / d;
+    Bi[1][0] = (B[1][2] * B[2][0] - B[1][0] * B[2][2]) / d;
+    Bi[1][1] = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) / d;
+    Bi[1][2] = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) / d;
+    Bi[2][0] = (B[1][0] * B[2][1] - B[1][1] * B[2][0]) / d;
+    Bi[2][1] = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) / d;
+    Bi[2][2] = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) / d;
+    return ORA_OK;
+}
+
+/* Mapped reference basis function k at xhat (unsigned): (1/det B) B eta_k
+ * (RT0, Eq. RT0piola) or B^-T eta_k (Nedelec, Ned0piola1). */
+static void mapped_basis(int kind, int dim, int k, const double* xh, double B[3][3], double Bi[3][3], double det,
+                         double phi[3])
+{
+    const affine_field* f = &ref_basis(kind, dim)[k];
+    double eta[3] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < dim; r++) {
+        eta[r] = f->a[r];
+        for (int c = 0; c < dim; c++) eta[r] += f->A[r][c] * xh[c];
+    }
+    for (int r = 0; r < 3; r++) phi[r] = 0.0;
+    for (int r = 0; r < dim; r++)
+        for (int c = 0; c < dim; c++) phi[r] += (kind == ORA_RT0) ? B[r][c] * eta[c] / det : Bi[c][r] * eta[c];
+}
+
+/* Load vector b_i = int F . eta_i by the collapsed Gauss-Legendre rule (n per
+ * direction): element by element in ascending order, b[dof_k] += s_k |det B|
+ * sum_q w_q F_q . phi_k(xhat_q). F: [q][element][dim] at ora_quad_points. */
+int ora_load_vector(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems, int n,
+                    const double* F, double* b)
+{
+    static qrule q;
+    ora_result topo;
+    if (!valid_kind(kind, dim)) return ORA_ERR_ARG;
+    int st = make_rule(dim, 1, n, &q);
+    if (st) return st;
+    st = ora_topology(kind, dim, V, nodes, T, elems, &topo);
+    if (st) return st;
+    int nl = nloc_of(kind, dim);
+    for (int64_t i = 0; i < topo.n_dofs; i++) b[i] = 0.0;
+    for (int64_t e = 0; e < T; e++) {
+        double P[4][3], B[3][3], Bi[3][3], det;
+        st = element_frame(dim, nodes, elems + e * (dim + 1), P, B, Bi, &det);
+        if (st) {
+            ora_free(&topo);
+            return st;
+        }
+        for (int k = 0; k < nl; k++) {
+            double acc = 0.0;
+            for (int i = 0; i < q.n; i++) {
+                double phi[3];
+                mapped_basis(kind, dim, k, q.x + 3 * i, B, Bi, det, phi);
+                double d = 0.0;
+                for (int c = 0; c < dim; c++) d += F[((int64_t)i * T + e) * dim + c] * phi[c];
+                acc += q.w[i] * d;
+            }
+            b[topo.elem2dof[e * nl + k]] += topo.sign[e * nl + k] * fabs(det) * acc;
+        }
+    }
+    ora_free(&topo);
+    return ORA_OK;
+}
+
+/* Values at the points of ora_quad_points of v_h = sum_k s_k v[dof_k] phi_k:
+ * out [q][element][dim]. */
+int ora_fe_values(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems, int n,
+                  const double* v, double* out)
+{
+    static qrule q;
+    ora_result topo;
+    if (!valid_kind(kind, dim)) return ORA_ERR_ARG;
+    int st = make_rule(dim, 1, n, &q);
+    if (st) return st;
+    st = ora_topology(kind, dim, V, nodes, T, elems, &topo);
+    if (st) return st;
+    int nl = nloc_of(kind, dim);
+    for (int64_t e = 0; e < T; e++) {
+        double P[4][3], B[3][3], Bi[3][3], det;
+        st = element_frame(dim, nodes, elems + e * (dim + 1), P, B, Bi, &det);
+        if (st) {
+            ora_free(&topo);
+            return st;
+        }
+        for (int i = 0; i < q.n; i++) {
+            double vh[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < nl; k++) {
+                double phi[3];
+                mapped_basis(kind, dim, k, q.x + 3 * i, B, Bi, det, phi);
+                double coef = topo.sign[e * nl + k] * v[topo.elem2dof[e * nl + k]];
+                for (int r = 0; r < dim; r++) vh[r] += coef * phi[r];
+            }
+            for (int r = 0; r < dim; r++) out[((int64_t)i * T + e) * dim + r] = vh[r];
+        }
+    }
+    ora_free(&topo);
+    return ORA_OK;
+}
+
+/* Per element: curl (Nedelec; Ned0piola2/3: curl eta / det B in 2D, B curl
+ * eta / det B in 3D) or divergence (RT0: div eta / det B) of v_h, from the
+ * derivatives of the reference basis. out: [T] or [T][3] (3D Nedelec). */
+int ora_fe_curl(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems, const double* v,
+                double* out)
+{
+    ora_result topo;
+    if (!valid_kind(kind, dim)) return ORA_ERR_ARG;
+    int st = ora_topology(kind, dim, V, nodes, T, elems, &topo);
+    if (st) return st;
+    const affine_field* basis = ref_basis(kind, dim);
+    int nl = nloc_of(kind, dim);
+    for (int64_t e = 0; e < T; e++) {
+        double P[4][3], B[3][3], Bi[3][3], det;
+        st = element_frame(dim, nodes, elems + e * (dim + 1), P, B, Bi, &det);
+        if (st) {
+            ora_free(&topo);
+            return st;
+        }
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < nl; k++) {
+            const affine_field* f = &basis[k];
+            double coef = topo.sign[e * nl + k] * v[topo.elem2dof[e * nl + k]];
+            if (kind == ORA_RT0) {
+                double dv = 0.0;
+                for (int r = 0; r < dim; r++) dv += f->A[r][r];
+                acc[0] += coef * dv / det;
+            } else if (dim == 2) {
+                acc[0] += coef * (f->A[1][0] - f->A[0][1]) / det;
+            } else {
+                double cr[3] = {f->A[2][1] - f->A[1][2], f->A[0][2] - f->A[2][0], f->A[1][0] - f->A[0][1]};
+                for (int r = 0; r < 3; r++)
+                    for (int c = 0; c < 3; c++) acc[r] += coef * B[r][c] * cr[c] / det;
+            }
+        }
+        if (kind == ORA_NED1 && dim == 3)
+            for (int r = 0; r < 3; r++) out[e * 3 + r] = acc[r];
+        else
+            out[e] = acc[0];
+    }
+    ora_free(&topo);
+    return ORA_OK;
+}

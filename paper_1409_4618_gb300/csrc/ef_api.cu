@@ -19,7 +19,8 @@ void free_plan_memory(ef_plan* p)
                     p->d_local,     p->d_status,     p->d_fb_slot_off, p->d_fb_sinfo, p->d_fb_cidx,
                     p->d_fb_posA,   p->d_fb_posB,    p->d_px_uid,
                     p->d_stage_nodes, p->d_stage_coeff, p->d_stage_K, p->d_stage_M,
-                    p->d_node_off,  p->d_node_inc,   p->d_adj_part,  p->d_adj_jpart, p->d_l2_part};
+                    p->d_node_off,  p->d_node_inc,   p->d_adj_part,  p->d_adj_jpart, p->d_l2_part,
+                    p->d_dof_off,   p->d_dof_inc,    p->d_load_local};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (cudaEvent_t e : p->copy_ev)

@@ -355,6 +355,186 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2(const int32_t* __restrict__ el
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// Physical basis functions at a point: phi_k(x) for the element's local DOFs
+// (unsigned). Nedelec: l_t grad l_h - l_h grad l_t (local edge t -> h);
+// RT0: (x - P_a(k)) / det B. xh: reference point; G: grad lambda_0..dim;
+// p: vertices; B: edge frame.
+template <int VAR>
+__device__ __forceinline__ void basis_at(const double* xh, const double (&G)[4][3], const double (&p)[4][3],
+                                         const double (&B)[3][3], double rdet, double (&phi)[6][3])
+{
+    constexpr int DIM = ElemTraits<VAR>::DIM;
+    constexpr int NL = ElemTraits<VAR>::NL;
+    if (VAR == NED2 || VAR == NED3) {
+        const double l[4] = {1.0 - xh[0] - xh[1] - xh[2], xh[0], xh[1], xh[2]};
+#pragma unroll
+        for (int k = 0; k < NL; k++) {
+            const int t = DIM == 3 ? kEdge3[k][0] : kEdge2[k][0];
+            const int h = DIM == 3 ? kEdge3[k][1] : kEdge2[k][1];
+#pragma unroll
+            for (int r = 0; r < 3; r++) phi[k][r] = fma(l[t], G[h][r], -(l[h] * G[t][r]));
+        }
+    } else {
+        double x[3];
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            double v = p[0][r];
+#pragma unroll
+            for (int i = 0; i < DIM; i++) v = fma(B[r][i], xh[i], v);
+            x[r] = v;
+        }
+#pragma unroll
+        for (int k = 0; k < NL; k++) {
+            const int a = DIM == 3 ? 3 - k : k;
+#pragma unroll
+            for (int r = 0; r < 3; r++) phi[k][r] = (x[r] - p[a][r]) * rdet;
+        }
+    }
+}
+
+// grad lambda_0 .. lambda_DIM: rows of B^-1 (cofactor columns / det).
+template <int DIM>
+__device__ __forceinline__ void barycentric_gradients(const double (&B)[3][3], double rdet, double (&G)[4][3])
+{
+    if (DIM == 3) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const int a = (i + 1) % 3, b = (i + 2) % 3;
+            G[i + 1][0] = fma(B[1][a], B[2][b], -(B[2][a] * B[1][b])) * rdet;
+            G[i + 1][1] = fma(B[2][a], B[0][b], -(B[0][a] * B[2][b])) * rdet;
+            G[i + 1][2] = fma(B[0][a], B[1][b], -(B[1][a] * B[0][b])) * rdet;
+        }
+    } else {
+        G[1][0] = B[1][1] * rdet;
+        G[1][1] = -B[0][1] * rdet;
+        G[2][0] = -B[1][0] * rdet;
+        G[2][1] = B[0][0] * rdet;
+        G[1][2] = G[2][2] = G[3][0] = G[3][1] = G[3][2] = 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; r++) G[0][r] = -(G[1][r] + G[2][r] + G[3][r]);
+}
+
+// Local load vectors l_k = s_k |det B| sum_q w_q F(x_q) . phi_k(x_q), F: [q][element][dim].
+template <int VAR>
+__global__ void __launch_bounds__(ITPB) k_load_local(const int32_t* __restrict__ elems,
+                                                     const double* __restrict__ nodes,
+                                                     const uint8_t* __restrict__ signbits,
+                                                     const double* __restrict__ F, int64_t T, Rule1D r,
+                                                     double* __restrict__ local, int* status)
+{
+    constexpr int DIM = ElemTraits<VAR>::DIM;
+    constexpr int NL = ElemTraits<VAR>::NL;
+    __shared__ double table[QMAX][4];
+    const int nq = fill_rule_table<DIM>(r, table);
+    const int64_t e = (int64_t)blockIdx.x * ITPB + threadIdx.x;
+    if (e >= T) return;
+    double p[4][3], B[3][3], G[4][3];
+    load_vertices<DIM>(elems, nodes, e, p);
+    const double det = edge_frame<DIM>(p, B);
+    if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+    const double rdet = 1.0 / det;
+    barycentric_gradients<DIM>(B, rdet, G);
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nq; q++) {
+        double phi[6][3];
+        basis_at<VAR>(table[q], G, p, B, rdet, phi);
+        const double* fq = F + ((int64_t)q * T + e) * DIM;
+        double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int c = 0; c < DIM; c++) f[c] = __ldg(fq + c);
+        const double wq = table[q][3];
+#pragma unroll
+        for (int k = 0; k < NL; k++) {
+            double d = 0.0;
+#pragma unroll
+            for (int c = 0; c < DIM; c++) d = fma(f[c], phi[k][c], d);
+            acc[k] = fma(wq, d, acc[k]);
+        }
+    }
+    const uint32_t neg = __ldg(signbits + e);
+    const double adet = fabs(det);
+#pragma unroll
+    for (int k = 0; k < NL; k++) {
+        const double v = adet * acc[k];
+        local[e * NL + k] = ((neg >> k) & 1u) ? -v : v;
+    }
+}
+
+// b[dof] = sum of its local entries in ascending element order (the DOF's
+// incidence segment: element * nl + k, sorted by DOF, stable in element).
+__global__ void __launch_bounds__(ITPB) k_load_sum(const uint32_t* __restrict__ off, const uint32_t* __restrict__ inc,
+                                                   const double* __restrict__ local, int64_t N,
+                                                   double* __restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * ITPB + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t s0 = off[i], s1 = off[i + 1];
+    double v = s1 > s0 ? local[inc[s0]] : 0.0;
+    for (uint32_t s = s0 + 1; s < s1; s++) v += local[inc[s]];
+    b[i] = v;
+}
+
+__global__ void k_dof_keys(const int32_t* __restrict__ e2d, int64_t n, uint64_t* keys, uint32_t* vals,
+                           uint32_t* cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * ITPB + threadIdx.x;
+    if (i >= n) return;
+    const int32_t d = e2d[i];
+    keys[i] = (uint64_t)d;
+    vals[i] = (uint32_t)i;   // element * nl + k
+    atomicAdd(&cnt[d], 1u);
+}
+
+// Per element, the constant curl of the Nedelec function of v, with
+// c_k = s_k v[dof_k] (Ned0piola3, curl phi_k = B curl eta_k / det B):
+//   2D: 2 / det B * sum_k c_k (every reference curl is 2);
+//   3D: 2 / det B * sum_k c_k w_k, w = (e3 - e2, e1 - e3, e2 - e1, e3, e1, e2)
+//   (B curl eta_k = 2 w_k, e_i the columns of B);
+// or the constant divergence of the RT0 function, dim / det B * sum_k c_k.
+template <int VAR>
+__global__ void __launch_bounds__(ITPB) k_fe_curl(const int32_t* __restrict__ elems,
+                                                  const double* __restrict__ nodes,
+                                                  const int32_t* __restrict__ e2d,
+                                                  const uint8_t* __restrict__ signbits,
+                                                  const double* __restrict__ v, int64_t T,
+                                                  double* __restrict__ out, int* status)
+{
+    constexpr int DIM = ElemTraits<VAR>::DIM;
+    constexpr int NL = ElemTraits<VAR>::NL;
+    const int64_t e = (int64_t)blockIdx.x * ITPB + threadIdx.x;
+    if (e >= T) return;
+    double p[4][3], B[3][3];
+    load_vertices<DIM>(elems, nodes, e, p);
+    const double det = edge_frame<DIM>(p, B);
+    if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+    const double rdet = 1.0 / det;
+    const uint32_t neg = __ldg(signbits + e);
+    double c[6];
+#pragma unroll
+    for (int k = 0; k < NL; k++) {
+        const double x = __ldg(v + __ldg(e2d + e * NL + k));
+        c[k] = ((neg >> k) & 1u) ? -x : x;
+    }
+    if (VAR == NED3) {
+        // B curl eta_k = 2 w_k, w = (e3 - e2, e1 - e3, e2 - e1, e3, e1, e2): curl phi_k = 2 w_k / det B
+        double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            const double w[6] = {B[r][2] - B[r][1], B[r][0] - B[r][2], B[r][1] - B[r][0], B[r][2], B[r][0], B[r][1]};
+#pragma unroll
+            for (int k = 0; k < 6; k++) s[r] = fma(c[k], w[k], s[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; r++) out[e * 3 + r] = 2.0 * s[r] * rdet;
+    } else {
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < NL; k++) sum += c[k];
+        out[e] = (VAR == RT3 ? 3.0 : 2.0) * sum * rdet;
+    }
+}
+
 // The partial sums in one fixed order: thread t adds t, t + 1024, ..., then a tree.
 __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ part, int64_t n, double* out)
 {
@@ -450,6 +630,94 @@ int ef_fe_values(const ef_plan* plan, const double* d_nodes, const double* d_v, 
         case RT3: k_fe_values<RT3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, plan->T, r, d_vals, plan->d_status); break;
         default: k_fe_values<NED3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, plan->T, r, d_vals, plan->d_status); break;
     }
+    EF_CUDA(cudaGetLastError());
+    return EF_OK;
+}
+
+int ef_fe_curl(const ef_plan* plan, const double* d_nodes, const double* d_v, double* d_out, void* stream)
+{
+    if (!plan) return EF_ERR_ARG;
+    if (plan->T == 0) return EF_OK;
+    if (!d_nodes || !d_v || !d_out) return EF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned g = (unsigned)((plan->T + ITPB - 1) / ITPB);
+    const int32_t* e2d = plan->d_elem2dof;
+    const uint8_t* sb = plan->d_signbits;
+    switch (plan->variant) {
+        case RT2: k_fe_curl<RT2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, plan->T, d_out, plan->d_status); break;
+        case NED2: k_fe_curl<NED2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, plan->T, d_out, plan->d_status); break;
+        case RT3: k_fe_curl<RT3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, plan->T, d_out, plan->d_status); break;
+        default: k_fe_curl<NED3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, plan->T, d_out, plan->d_status); break;
+    }
+    EF_CUDA(cudaGetLastError());
+    return EF_OK;
+}
+
+int ef_load_vector(ef_plan* plan, const double* d_nodes, int n, const double* d_F, double* d_b, void* stream)
+{
+    if (!plan) return EF_ERR_ARG;
+    Rule1D r;
+    int nq = 0;
+    EF_TRY(make_rule(plan->dim, n, &r, &nq));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->N > 0 && !d_b) return EF_ERR_ARG;
+    if (plan->T == 0) {
+        if (plan->N > 0) EF_CUDA(cudaMemsetAsync(d_b, 0, (size_t)plan->N * sizeof(double), s));
+        return EF_OK;
+    }
+    if (!d_nodes || !d_F) return EF_ERR_ARG;
+    const int64_t nl = plan->nl, n_inc = plan->T * nl;
+    if (!plan->d_dof_inc) {
+        // DOF -> (element, local DOF) incidence, ascending element order inside a DOF
+        uint64_t* keys = nullptr;
+        uint32_t* cnt = nullptr;
+        void* tmp = nullptr;
+        size_t tb = radix_tmp_bytes(n_inc);
+        if (scan_tmp_bytes(plan->N) > tb) tb = scan_tmp_bytes(plan->N);
+        int st = EF_OK;
+        if (cudaMalloc((void**)&plan->d_dof_inc, n_inc * 4) != cudaSuccess ||
+            cudaMalloc((void**)&plan->d_dof_off, (plan->N + 1) * 4) != cudaSuccess ||
+            cudaMalloc((void**)&plan->d_load_local, n_inc * 8) != cudaSuccess ||
+            cudaMalloc((void**)&keys, n_inc * 8) != cudaSuccess || cudaMalloc((void**)&cnt, plan->N * 4) != cudaSuccess ||
+            cudaMalloc(&tmp, tb) != cudaSuccess) {
+            set_last_error("cudaMalloc(load vector)", cudaErrorMemoryAllocation);
+            st = EF_ERR_OOM;
+        }
+        if (st == EF_OK) {
+            cudaMemsetAsync(cnt, 0, plan->N * 4, s);
+            k_dof_keys<<<(unsigned)((n_inc + ITPB - 1) / ITPB), ITPB, 0, s>>>(plan->d_elem2dof, n_inc, keys,
+                                                                              plan->d_dof_inc, cnt);
+            st = radix_sort_pairs(keys, plan->d_dof_inc, n_inc, bits_for((uint64_t)plan->N), tmp, s);
+            if (st == EF_OK) st = exclusive_scan_u32(cnt, plan->d_dof_off, plan->N, true, tmp, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (st == EF_OK && e != cudaSuccess) {
+                set_last_error("ef_load_vector incidence", e);
+                st = EF_ERR_CUDA;
+            }
+        }
+        cudaFree(keys);
+        cudaFree(cnt);
+        cudaFree(tmp);
+        if (st != EF_OK) {
+            cudaFree(plan->d_dof_inc);
+            cudaFree(plan->d_dof_off);
+            cudaFree(plan->d_load_local);
+            plan->d_dof_inc = plan->d_dof_off = nullptr;
+            plan->d_load_local = nullptr;
+            return st;
+        }
+    }
+    const unsigned g = (unsigned)((plan->T + ITPB - 1) / ITPB);
+    const uint8_t* sb = plan->d_signbits;
+    double* loc = plan->d_load_local;
+    switch (plan->variant) {
+        case RT2: k_load_local<RT2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_F, plan->T, r, loc, plan->d_status); break;
+        case NED2: k_load_local<NED2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_F, plan->T, r, loc, plan->d_status); break;
+        case RT3: k_load_local<RT3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_F, plan->T, r, loc, plan->d_status); break;
+        default: k_load_local<NED3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_F, plan->T, r, loc, plan->d_status); break;
+    }
+    k_load_sum<<<(unsigned)((plan->N + ITPB - 1) / ITPB), ITPB, 0, s>>>(plan->d_dof_off, plan->d_dof_inc, loc, plan->N,
+                                                                         d_b);
     EF_CUDA(cudaGetLastError());
     return EF_OK;
 }

@@ -144,6 +144,11 @@ struct ef_plan {
 
     // per-CTA partial norms of ef_norm_l2 (allocated on first use)
     double* d_l2_part;
+    // ef_load_vector (allocated on first use): DOF -> (element * nl + k)
+    // incidence in ascending element order, and the local load vectors
+    uint32_t* d_dof_off;
+    uint32_t* d_dof_inc;
+    double* d_load_local;
 };
 
 namespace ef {

@@ -120,6 +120,8 @@ def load():
             "ef_quad_points": ([P, P, I, P, P], I),
             "ef_fe_values": ([P, P, P, I, P, P], I),
             "ef_norm_l2": ([P, P, I, I, P, P, P, P, P], I),
+            "ef_fe_curl": ([P, P, P, P, P], I),
+            "ef_load_vector": ([P, P, I, P, P, P], I),
             "ef_status_string": ([I], C.c_char_p),
             "ef_last_error": ([], C.c_char_p),
         }
@@ -386,6 +388,23 @@ class Plan:
         _check(load().ef_fe_values(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(v, torch.float64, "v"),
                                    int(n), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
+
+    def fe_curl(self, nodes, v, stream=None):
+        """Per-element curl (Nedelec: [n_elems] in 2D, [n_elems, 3] in 3D) or divergence (RT0: [n_elems])."""
+        shape = (self.n_elems, 3) if (self.kind == EF_NED1 and self.dim == 3) else (self.n_elems,)
+        out = torch.empty(shape, dtype=torch.float64, device=self.device)
+        _check(load().ef_fe_curl(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(v, torch.float64, "v"),
+                                 C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def load_vector(self, nodes, F, n: int, stream=None):
+        """b_i = int F . eta_i, F given at the quadrature points [nq, n_elems, dim]."""
+        if not F.is_contiguous():
+            raise TypeError("F must be contiguous")
+        b = torch.empty(self.n_dofs, dtype=torch.float64, device=self.device)
+        _check(load().ef_load_vector(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
+                                     _dev(F, torch.float64, "F"), C.c_void_p(b.data_ptr()), _stream_ptr(stream)))
+        return b
 
     def norm_l2(self, nodes, f, n: int, v=None, per_element: bool = False, stream=None):
         """Squared L2 norm of f (values [nq, n_elems, ncomp] at the quadrature points), minus the FE

@@ -1,0 +1,99 @@
+"""The paper's Table 5 through the GPU library (needs a GB300).
+
+K + M, the load vector of F, the error norms and the per-element curls all
+come from the C ABI (ef_assemble, ef_quad_points, ef_load_vector,
+ef_norm_l2, ef_fe_curl); scipy solves the Galerkin system on the host. The
+energy errors must equal the printed ones to their last digit. Also: the load
+vector and the per-element curls against the oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1409_4618_gb300 import meshgen as mg
+from tests._eddy import exact, rhs
+from tests.test_oracle_eddy import _levels
+from tests.test_oracle_integration import _affine, _linear_dofs
+
+pytestmark = pytest.mark.gpu
+
+RT0, NED1 = 1, 2
+CASES = [(RT0, 2), (NED1, 2), (RT0, 3), (NED1, 3)]
+
+
+def eddy_error_gpu(m, n=6):
+    import scipy.sparse as sps
+    import scipy.sparse.linalg as spla
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_square(m)
+    dev = torch.device("cuda")
+    tn = torch.from_numpy(nodes).to(dev)
+    plan = ef.Plan(NED1, 2, nodes.shape[0], torch.from_numpy(elems).to(dev))
+    K, M = plan.assemble(tn, None)
+    rowptr, colidx = plan.pattern()
+    x = plan.quad_points(tn, n).cpu().numpy()
+    cen = nodes[elems].mean(1)
+    inside = np.broadcast_to(cen[:, 0] > cen[:, 1], x.shape[:2])
+    F1, F2 = rhs(x[..., 0], x[..., 1], inside)
+    b = plan.load_vector(tn, torch.from_numpy(np.ascontiguousarray(np.stack([F1, F2], -1))).to(dev), n)
+    N = plan.n_dofs
+    A = sps.csr_matrix(((K + M).cpu().numpy(), colidx.cpu().numpy(), rowptr.cpu().numpy()), shape=(N, N))
+    v = torch.from_numpy(spla.spsolve(A.tocsc(), b.cpu().numpy())).to(dev)
+    E1, E2, curlE = exact(x[..., 0], x[..., 1], inside)
+    l2, _ = plan.norm_l2(tn, torch.from_numpy(np.ascontiguousarray(np.stack([E1, E2], -1))).to(dev), n, v=v)
+    cv = plan.fe_curl(tn, v).cpu().numpy()
+    dc = torch.from_numpy(np.ascontiguousarray((curlE - cv[None, :])[..., None])).to(dev)
+    c2, _ = plan.norm_l2(tn, dc, n)
+    plan.check()
+    plan.close()
+    return N, float(np.sqrt(float(l2) + float(c2)))
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_table5_energy_errors_gpu(level):
+    lv = _levels()[level]
+    N, err = eddy_error_gpu(lv["m"])
+    assert N == lv["edges"]
+    assert abs(err - lv["error"]) <= 1e-6 * lv["error"]
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_load_vector_and_curl_parity(ora, kind, dim):
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(7, 0.2, 47) if dim == 3 else mg.kuhn_square(19, 0.2, 47)
+    elems = mg.shuffle_local_order(elems, 147)
+    dev = torch.device("cuda")
+    tn = torch.from_numpy(nodes).to(dev)
+    plan = ef.Plan(kind, dim, nodes.shape[0], torch.from_numpy(elems).to(dev))
+    A, c = _affine(dim, 47)
+    n = 3
+    xg = plan.quad_points(tn, n).cpu().numpy()
+    bg = plan.load_vector(tn, torch.from_numpy(np.ascontiguousarray(xg @ A.T + c)).to(dev), n).cpu().numpy()
+    xo = ora.quad_points(dim, nodes, elems, n)
+    bo = ora.load_vector(kind, dim, nodes, elems, n, xo @ A.T + c)
+    assert np.max(np.abs(bg - bo)) <= 1e-12 * np.max(np.abs(bo))
+    v = mg.normal(47, mg.STREAM_V, plan.n_dofs)
+    cg = plan.fe_curl(tn, torch.from_numpy(v).to(dev)).cpu().numpy()
+    co = ora.fe_curl(kind, dim, nodes, elems, v)
+    assert np.max(np.abs(cg - co)) <= 1e-12 * np.max(np.abs(co))
+    # the interpolant of an affine field: exact curl / divergence on every element
+    d2n = plan.topology()[2].cpu().numpy()
+    u = torch.from_numpy(_linear_dofs(kind, dim, nodes, d2n, A, c)).to(dev)
+    cu = plan.fe_curl(tn, u).cpu().numpy()
+    if kind == RT0:
+        expect = np.trace(A)
+    elif dim == 2:
+        expect = A[1, 0] - A[0, 1]
+    else:
+        expect = np.array([A[2, 1] - A[1, 2], A[0, 2] - A[2, 0], A[1, 0] - A[0, 1]])
+    assert np.max(np.abs(cu - expect)) < 1e-11 * (1 + np.abs(A).max())
+    # load vector sums repeat bit for bit
+    b2 = plan.load_vector(tn, torch.from_numpy(np.ascontiguousarray(xg @ A.T + c)).to(dev), n).cpu().numpy()
+    assert np.array_equal(bg.view(np.uint64), b2.view(np.uint64))
+    plan.check()
+    plan.close()

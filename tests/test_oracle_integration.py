@@ -109,3 +109,66 @@ def test_oracle_interpolant_of_constant_is_exact(ora, kind, dim):
     zero = np.zeros_like(cf)
     energy, _ = ora.norm_l2(kind, dim, nodes, elems, n, zero, u)
     assert abs(energy - c @ c) < 1e-13
+
+
+def _linear_dofs(kind, dim, nodes, d2n, A, c):
+    """DOFs of the affine field E(x) = A x + c: edge line integrals (Nedelec,
+    from the larger to the smaller node id), edge fluxes through R_cw(X_a - X_b)
+    (2D RT0), and N_f . E(centroid) with N_f = (X_b - X_a) x (X_c - X_a) (3D
+    RT0, the printed basis of flux 1/2), all exact for affine E."""
+    E = lambda x: x @ A.T + c
+    Xa, Xb = nodes[d2n[:, 0]], nodes[d2n[:, 1]]
+    if kind == NED1:
+        return np.einsum("ij,ij->i", E(0.5 * (Xa + Xb)), Xa - Xb)
+    if dim == 2:
+        t = Xa - Xb
+        return np.einsum("ij,ij->i", E(0.5 * (Xa + Xb)), np.stack([t[:, 1], -t[:, 0]], 1))
+    Xc = nodes[d2n[:, 2]]
+    return np.einsum("ij,ij->i", E((Xa + Xb + Xc) / 3.0), np.cross(Xb - Xa, Xc - Xa))
+
+
+def _affine(dim, seed):
+    A = mg.normal(seed, 12, dim * dim).reshape(dim, dim)
+    return A, mg.normal(seed, 13, dim)
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_oracle_load_vector_pins(ora, kind, dim):
+    """b . v = int F . v_h: for F = c and v its interpolant, |Omega| |c|^2;
+    for F = v_h(u), b = M u (mass matrix, unit coefficient)."""
+    nodes, elems = _mesh(dim, 3, 37)
+    r = ora.assemble(kind, dim, nodes, elems)
+    n = 3
+    c = np.array([0.7, -1.3, 0.4])[:dim]
+    cf = np.broadcast_to(c, (n ** dim, elems.shape[0], dim)).copy()
+    b = ora.load_vector(kind, dim, nodes, elems, n, cf)
+    u_c = _constant_dofs(kind, dim, nodes, r["dof2nodes"], c)
+    assert abs(b @ u_c - c @ c) < 1e-13
+    u = mg.normal(37, mg.STREAM_U, r["n_dofs"])
+    vh = ora.fe_values(kind, dim, nodes, elems, n, u)
+    b2 = ora.load_vector(kind, dim, nodes, elems, n, vh)
+    Mu = to_dense(r, "M") @ u
+    assert np.max(np.abs(b2 - Mu)) < 1e-13 * np.max(np.abs(Mu))
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_oracle_curl_of_interpolant_is_exact(ora, kind, dim):
+    """The interpolant of an affine field has the field's constant curl (or
+    divergence) on every element (commuting diagram)."""
+    nodes, elems = _mesh(dim, 3, 39)
+    topo = ora.topology(kind, dim, nodes, elems)
+    A, c = _affine(dim, 39)
+    u = _linear_dofs(kind, dim, nodes, topo["dof2nodes"], A, c)
+    got = ora.fe_curl(kind, dim, nodes, elems, u)
+    if kind == RT0:
+        expect = np.trace(A)
+    elif dim == 2:
+        expect = A[1, 0] - A[0, 1]
+    else:
+        expect = np.array([A[2, 1] - A[1, 2], A[0, 2] - A[2, 0], A[1, 0] - A[0, 1]])
+    assert np.max(np.abs(got - expect)) < 1e-12 * (1 + np.abs(A).max())
+    # lowest-order elements reproduce constants only: the interpolation error
+    # of the affine field at the points is first order, bounded by about h |A|
+    vals = ora.fe_values(kind, dim, nodes, elems, 2, u)
+    x = ora.quad_points(dim, nodes, elems, 2)
+    assert np.abs(vals - (x @ A.T + c)).max() < 2.0 * np.abs(A).sum() / 3
