@@ -231,11 +231,13 @@ def run_batched(args, dev, plain_rate):
     batch.check()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    _nvtx(torch, "timed")
     e0.record(stream)
     for _ in range(args.batch_steps):
         batch.assemble(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    _nvtx(torch, None)
     batch.check()
     ms = e0.elapsed_time(e1) / args.batch_steps
     T = int(sum(batch.n_elems))
@@ -327,11 +329,13 @@ def run_integration(args, dev, peaks):
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = args.integration_steps
+    _nvtx(torch, "timed")
     a.record(stream)
     for _ in range(steps):
         plan.norm_l2(tn, f, n, v=v, per_element=True)
     b.record(stream)
     torch.cuda.synchronize()
+    _nvtx(torch, None)
     plan.check()
     ms = a.elapsed_time(b) / steps
     T, V = elems.shape[0], nodes.shape[0]
@@ -355,7 +359,7 @@ def run_adjoint(args, dev):
 
     from paper_1409_4618_gb300 import edgefem as ef
 
-    nodes, elems = mg.kuhn_cube(96, 0.2, 5)
+    nodes, elems = mg.kuhn_cube(args.adjoint_cube, 0.2, 5)
     coeff = mg.log_uniform_coeff(5, elems.shape[0])
     tn, tc = torch.from_numpy(nodes).to(dev), torch.from_numpy(coeff).to(dev)
     plan = ef.Plan(2, 3, nodes.shape[0], torch.from_numpy(elems).to(dev))
@@ -373,11 +377,13 @@ def run_adjoint(args, dev):
             fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _nvtx(torch, "timed")
         a.record(stream)
         for _ in range(steps):
             fn()
         b.record(stream)
         torch.cuda.synchronize()
+        _nvtx(torch, None)
         return a.elapsed_time(b) / steps
 
     ms_adj = timed(lambda: ef.ef_adjoint(plan.handle, tn, tc, u, v, J, gx, gs, stream), args.adjoint_steps)
@@ -385,7 +391,7 @@ def run_adjoint(args, dev):
     plan.check()
     T = elems.shape[0]
     ops = ADJOINT_FP64_OPS_PER_TET * T
-    out = {"value": T / (ms_adj / 1e3) / 1e6, "unit": UNIT, "workload": "ned3d_kuhn96_jitter0.2",
+    out = {"value": T / (ms_adj / 1e3) / 1e6, "unit": UNIT, "workload": f"ned3d_kuhn{args.adjoint_cube}_jitter0.2",
            "elements": int(T), "ms_per_step": ms_adj,
            "plain_same_mesh": {"value": T / (ms_asm / 1e3) / 1e6, "ms_per_step": ms_asm},
            "vs_plain": ms_asm / ms_adj,
@@ -419,6 +425,14 @@ def run_gpu(args):
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.only:
+        # one workload by itself (for profiling): its JSON object on one line
+        dev = torch.device("cuda", local)
+        peaks, _ = _peaks()
+        legs = {"batched": lambda: run_batched(args, dev, float("nan")), "adjoint": lambda: run_adjoint(args, dev),
+                "rt0": lambda: run_rt0(args, dev, peaks), "integration": lambda: run_integration(args, dev, peaks)}
+        print(json.dumps({"leg": args.only, **legs[args.only]()}), flush=True)
+        return 0
     dist = None
     if ws > 1:
         import torch.distributed as dist
@@ -590,6 +604,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rt0", action="store_true")
+    ap.add_argument("--only", choices=["batched", "adjoint", "rt0", "integration"],
+                    help="run one of the other workloads by itself (profiling)")
+    ap.add_argument("--adjoint-cube", type=int, default=96)
     ap.add_argument("--no-integration", action="store_true")
     ap.add_argument("--integration-steps", type=int, default=50)
     ap.add_argument("--rt0-steps", type=int, default=20)
