@@ -118,6 +118,18 @@ int ef_plan_set_block(ef_plan* plan, int block, void* stream);
  * work-order arrays. */
 int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream);
 
+/* Fault injection for tests of the bounded waits (the paper has no such
+ * step). With on != 0, the next calls of ef_assemble on the one-launch queue
+ * selected by ef_plan_set_pipeline wait for an element tile that never
+ * completes: each waiting sum tile gives up after at most about one second
+ * of wall time (a CTA stops waiting as soon as another has given up), skips
+ * its sums, and ef_plan_check returns EF_ERR_TIMEOUT. The GPU stays usable;
+ * K and M of such a call are incomplete. on = 0 restores the schedule, as
+ * does any later ef_plan_set_pipeline or ef_plan_tune. Synchronises
+ * `stream`. Errors: EF_ERR_ARG if the plan has no queue schedule, or (on !=
+ * 0) if another schedule is selected. */
+int ef_plan_inject_stall(ef_plan* plan, int on, void* stream);
+
 /* Autotuner for ef_assemble on this plan: times `reps` calls of each
  * candidate on the given buffers and keeps the fastest: the plain two-pass
  * kernels (*chosen = 0); the one-launch persistent queue with 4, 8 or 16

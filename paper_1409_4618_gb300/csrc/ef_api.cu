@@ -266,6 +266,13 @@ int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream)
     return EF_OK;
 }
 
+int ef_plan_inject_stall(ef_plan* plan, int on, void* stream)
+{
+    if (!plan || !plan->queue) return EF_ERR_ARG;
+    if (on && (plan->use_two_pass || plan->use_blocked)) return EF_ERR_ARG;
+    return queue_inject_stall(plan->queue, on, (cudaStream_t)stream);
+}
+
 int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
                  int reps, int* chosen, void* stream)
 {

@@ -43,19 +43,17 @@ template <int VAR>
 __device__ __forceinline__ void element_body(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
                                              const double* __restrict__ coeffK, const double* __restrict__ coeffM,
                                              const uint32_t* __restrict__ inv, int64_t e, int64_t T,
-                                             double* __restrict__ list, int* status)
+                                             double2* __restrict__ list, int* status)
 {
     using E = ElemTraits<VAR>;
     double Kq[E::NP], Mq[E::NP];
     const double sigmaK = coeffK ? __ldg(coeffK + e) : 1.0;
     const double sigmaM = coeffM == coeffK ? sigmaK : (coeffM ? __ldg(coeffM + e) : 1.0);
     if (compute_element<VAR>(elems, nodes, sigmaK, sigmaM, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
-    const int64_t nK = (int64_t)E::NP * T;
 #pragma unroll
     for (int q = 0; q < E::NP; q++) {
         const uint32_t pos = __ldg(inv + (int64_t)q * T + e);
-        list[pos] = Kq[q];
-        list[nK + pos] = Mq[q];
+        list[pos] = make_double2(Kq[q], Mq[q]);
     }
 }
 
@@ -65,7 +63,7 @@ __global__ void __launch_bounds__(EPB, 6) k_element_local(const int32_t* __restr
                                                        const double* __restrict__ coeffK,
                                                        const double* __restrict__ coeffM,
                                                        const uint32_t* __restrict__ inv, int64_t e0, int64_t e1,
-                                                       int64_t T, double* __restrict__ list, int* status)
+                                                       int64_t T, double2* __restrict__ list, int* status)
 {
     const int64_t e = e0 + (int64_t)blockIdx.x * EPB + threadIdx.x;
     if (e >= e1) return;
@@ -158,8 +156,8 @@ __device__ __forceinline__ void scatter_body(int64_t base, int64_t w0, int64_t w
                                              const uint32_t* __restrict__ wseg, const uint32_t* __restrict__ wpos_up,
                                              const uint32_t* __restrict__ wpos_lo,
                                              const StoreIdx* __restrict__ st_up, const StoreIdx* __restrict__ st_lo,
-                                             const double* __restrict__ listK, const double* __restrict__ listM,
-                                             double* __restrict__ K, double* __restrict__ M)
+                                             const double2* __restrict__ list, double* __restrict__ K,
+                                             double* __restrict__ M)
 {
     __shared__ double sk[SB], sm[SB];
     __shared__ uint32_t su[SB], sl[SB];
@@ -169,10 +167,12 @@ __device__ __forceinline__ void scatter_body(int64_t base, int64_t w0, int64_t w
         const uint32_t s0 = wseg[i], s1 = wseg[i + 1];
         su[t] = wpos_up[i];
         sl[t] = wpos_lo[i];
-        double k = listK[s0], m = listM[s0];
+        double2 v = list[s0];
+        double k = v.x, m = v.y;
         for (uint32_t s = s0 + 1; s < s1; s++) {
-            k += listK[s];
-            m += listM[s];
+            v = list[s];
+            k += v.x;
+            m += v.y;
         }
         sk[t] = k;
         sm[t] = m;
@@ -199,10 +199,10 @@ __global__ void __launch_bounds__(SB) k_scatter(int64_t w0, int64_t w1, int64_t 
                                                 const uint32_t* __restrict__ wpos_up,
                                                 const uint32_t* __restrict__ wpos_lo,
                                                 const StoreIdx* __restrict__ st_up, const StoreIdx* __restrict__ st_lo,
-                                                const double* __restrict__ listK, const double* __restrict__ listM,
-                                                double* __restrict__ K, double* __restrict__ M)
+                                                const double2* __restrict__ list, double* __restrict__ K,
+                                                double* __restrict__ M)
 {
-    scatter_body((w0 / SB + blockIdx.x) * SB, w0, w1, U, wseg, wpos_up, wpos_lo, st_up, st_lo, listK, listM, K, M);
+    scatter_body((w0 / SB + blockIdx.x) * SB, w0, w1, U, wseg, wpos_up, wpos_lo, st_up, st_lo, list, K, M);
 }
 
 // The sum over every mesh of a batch: CTA b takes the SB-block of work items
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(SB, 8) k_batch_scatter(const QueueMesh* __rest
     __shared__ int64_t first;
     const int64_t base = load_block_mesh(md, blk_mesh, blk_off, d, &first) * SB;
     scatter_body(base, 0, d.U, d.U, d.wseg, d.wpos_up, d.wpos_lo, (const StoreIdx*)d.wst_up,
-                 (const StoreIdx*)d.wst_lo, d.list, d.list + (int64_t)NP * d.T, d.K, d.M);
+                 (const StoreIdx*)d.wst_lo, d.list, d.K, d.M);
 }
 
 // Store-order keys: block of the work item, then its CSR position.
@@ -290,10 +290,10 @@ int element_range(const ef_plan* p, const double* nodes, const double* cK, const
     if (e1 <= e0) return EF_OK;
     const unsigned grid = (unsigned)((e1 - e0 + EPB - 1) / EPB);
     switch (p->variant) {
-        case RT2: k_element_local<RT2><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        case NED2: k_element_local<NED2><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        case RT3: k_element_local<RT3><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
-        default: k_element_local<NED3><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, p->d_local, p->d_status); break;
+        case RT2: k_element_local<RT2><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, (double2*)p->d_local, p->d_status); break;
+        case NED2: k_element_local<NED2><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, (double2*)p->d_local, p->d_status); break;
+        case RT3: k_element_local<RT3><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, (double2*)p->d_local, p->d_status); break;
+        default: k_element_local<NED3><<<grid, EPB, 0, s>>>(p->d_elems, nodes, cK, cM, p->d_inv, e0, e1, p->T, (double2*)p->d_local, p->d_status); break;
     }
     EF_CUDA(cudaGetLastError());
     return EF_OK;
@@ -303,10 +303,8 @@ int scatter_range(const ef_plan* p, int64_t w0, int64_t w1, double* K, double* M
 {
     if (w1 <= w0) return EF_OK;
     const unsigned grid = (unsigned)((w1 - 1) / SB - w0 / SB + 1);
-    const double* lK = p->d_local;
-    const double* lM = p->d_local + (int64_t)p->np * p->T;
     k_scatter<<<grid, SB, 0, s>>>(w0, w1, p->U, p->d_wseg, p->d_wpos_up, p->d_wpos_lo, (const StoreIdx*)p->d_wst_up,
-                                  (const StoreIdx*)p->d_wst_lo, lK, lM, K, M);
+                                  (const StoreIdx*)p->d_wst_lo, (const double2*)p->d_local, K, M);
     EF_CUDA(cudaGetLastError());
     return EF_OK;
 }

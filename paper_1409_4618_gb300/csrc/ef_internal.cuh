@@ -103,7 +103,7 @@ struct ef_plan {
     uint32_t* d_wpos_lo;  // U: CSR position of (c, r), or 0xffffffff
     void* d_wst_up;       // U: per block of sum items (ef_assemble.cu), the items in ascending (r, c) position
     void* d_wst_lo;       // U: per block of sum items, the items in ascending (c, r) position
-    double* d_local;      // 2 * np * T: contribution list (K then M values) of the two-pass paths
+    double* d_local;      // 2 * np * T: contribution list of the two-pass paths, (K, M) pairs in work order
     int* d_status;        // device status word
 
     // fused path (blocks of fb_block consecutive elements): see ef_fused.cu

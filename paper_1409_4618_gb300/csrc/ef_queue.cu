@@ -34,7 +34,20 @@
 namespace ef {
 namespace {
 
-constexpr unsigned kPollLimit = 20000000u;   // ~2-3 s of polling with back-off
+// A sum tile gives up waiting after kWaitNs of wall time (the GPU's global
+// nanosecond timer) or kPollLimit polls, whichever comes first, sets the
+// timeout status and skips its work; once any tile has given up, the others
+// see the status within 64 polls and give up too. Legitimate waits last at
+// most the element work of a few chunks (milliseconds).
+constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr unsigned kPollLimit = 50000000u;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // CTAs per SM the kernel is compiled for: 80 registers per thread, enough for
 // the 3D Nedelec element matrices without spills.
@@ -96,12 +109,10 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
                 double Kq[E::NP], Mq[E::NP];
                 const double sigma = coeff ? __ldg(coeff + e) : 1.0;
                 if (compute_element<VAR>(d.elems, nodes, sigma, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
-                const int64_t nK = (int64_t)E::NP * d.T;
 #pragma unroll
                 for (int q = 0; q < E::NP; q++) {
                     const uint32_t p = __ldg(d.inv + (int64_t)q * d.T + e);
-                    d.list[p] = Kq[q];
-                    d.list[nK + p] = Mq[q];
+                    d.list[p] = make_double2(Kq[q], Mq[q]);
                 }
             }
             __syncthreads();
@@ -113,9 +124,16 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
             if (threadIdx.x == 0) {
                 int ok = 1;
                 unsigned polls = 0;
+                uint64_t t0 = 0;
                 for (int j = g.dep_first; j < g.dep_first + g.dep_count && ok; j++) {
                     while (atomicAdd(&done[j], 0u) < need[j]) {
-                        if (++polls > kPollLimit) {
+                        if (polls == 0) t0 = global_ns();
+                        ++polls;
+                        if ((polls & 63u) == 0 && (*(volatile int*)status & ST_TIMEOUT)) {
+                            ok = 0;
+                            break;
+                        }
+                        if (polls > kPollLimit || global_ns() - t0 > kWaitNs) {
                             ok = 0;
                             atomicOr(status, ST_TIMEOUT);
                             break;
@@ -130,17 +148,18 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
             if (s_ok) {
                 double* K = nodes0 ? K0 : d.K;
                 double* M = nodes0 ? M0 : d.M;
-                const double* lK = d.list;
-                const double* lM = d.list + (int64_t)E::NP * d.T;
+                const double2* l = d.list;
                 const int64_t i0 = g.lo + t * BU;
                 const int64_t i1 = i0 + BU < g.hi ? i0 + BU : g.hi;
                 for (int64_t i = i0 + threadIdx.x; i < i1; i += BE) {
                     const uint32_t s0 = d.wseg[i], s1 = d.wseg[i + 1];
                     const uint32_t pu = d.wpos_up[i], pl = d.wpos_lo[i];
-                    double kv = __ldcg(lK + s0), mv = __ldcg(lM + s0);
+                    double2 v = __ldcg(l + s0);
+                    double kv = v.x, mv = v.y;
                     for (uint32_t s = s0 + 1; s < s1; s++) {
-                        kv += __ldcg(lK + s);
-                        mv += __ldcg(lM + s);
+                        v = __ldcg(l + s);
+                        kv += v.x;
+                        mv += v.y;
                     }
                     K[pu] = kv;
                     M[pu] = mv;
@@ -345,6 +364,7 @@ int queue_build(Queue* q, const std::vector<ef_plan*>& plans, cudaStream_t s)
     if (q->nseg > 0)
         EF_CUDA(cudaMemcpyAsync(q->d_seg, segs.data(), sizeof(QueueSegment) * q->nseg, cudaMemcpyHostToDevice, s));
     if (N > 0) EF_CUDA(cudaMemcpyAsync(q->d_need, need.data(), sizeof(uint32_t) * N, cudaMemcpyHostToDevice, s));
+    q->stall = 0;
     EF_CUDA(cudaMemsetAsync(q->d_ctrl, 0, sizeof(uint32_t) * (N + 3), s));
     EF_CUDA(cudaStreamSynchronize(s));
     return EF_OK;
@@ -368,7 +388,7 @@ int queue_set_meshes(Queue* q, const std::vector<ef_plan*>& plans, cudaStream_t 
         d.wpos_lo = p->d_wpos_lo;
         d.wst_up = p->d_wst_up;
         d.wst_lo = p->d_wst_lo;
-        d.list = p->d_local;
+        d.list = (double2*)p->d_local;
         d.T = p->T;
         d.U = p->U;
         d.nodes = keep_nodes;
@@ -448,6 +468,25 @@ int queue_check(const Queue* q, cudaStream_t s)
     if (st) EF_CUDA(cudaMemsetAsync(q->d_status, 0, sizeof(int), s));
     if (st & ST_TIMEOUT) return EF_ERR_TIMEOUT;
     if (st & ST_DEGENERATE) return EF_ERR_DEGENERATE;
+    return EF_OK;
+}
+
+// Fault injection: raise (on) or restore (!on) the number of element tiles
+// that the first element chunk must report done. Raised, the sums that
+// depend on that chunk wait for a tile that never comes, give up after the
+// wait limit, and the launch ends with the timeout status.
+int queue_inject_stall(Queue* q, int on, cudaStream_t s)
+{
+    if (!q->d_need || q->nctr < 1) return EF_ERR_ARG;
+    const uint32_t want = on ? 1u : 0u;
+    if (want == q->stall) return EF_OK;
+    uint32_t n0 = 0;
+    EF_CUDA(cudaMemcpyAsync(&n0, q->d_need, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    EF_CUDA(cudaStreamSynchronize(s));
+    n0 = n0 - q->stall + want;
+    EF_CUDA(cudaMemcpyAsync(q->d_need, &n0, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    EF_CUDA(cudaStreamSynchronize(s));
+    q->stall = want;
     return EF_OK;
 }
 

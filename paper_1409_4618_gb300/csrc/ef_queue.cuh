@@ -16,7 +16,7 @@ struct QueueMesh {              // device-side view of one mesh's plan
     const uint32_t* wpos_lo;    // work item -> CSR position of (c,r) or 0xffffffff
     const void* wst_up;         // store orders of the sum kernel (ef_assemble.cu)
     const void* wst_lo;
-    double* list;               // 2 * np * T contribution values
+    double2* list;              // np * T contribution values, (K, M) pairs
     const double* nodes;        // bound buffers (batch); the single-mesh path passes them per call
     const double* coeff;
     double* K;
@@ -67,6 +67,7 @@ struct Queue {
     int64_t n_eblk = 0, n_sblk = 0;
     int64_t cap_eblk = 0, cap_sblk = 0;
     int nmesh = 0;
+    uint32_t stall = 0;           // fault injection: extra tiles the first element chunk must report
 };
 
 int queue_init(Queue* q, int variant, int* shared_status);
@@ -75,6 +76,7 @@ int queue_set_meshes(Queue* q, const std::vector<ef_plan*>& plans, cudaStream_t 
 int queue_build(Queue* q, const std::vector<ef_plan*>& plans, cudaStream_t s);
 int queue_launch(const Queue* q, const QueueArgs& a, cudaStream_t s);
 int queue_check(const Queue* q, cudaStream_t s);
+int queue_inject_stall(Queue* q, int on, cudaStream_t s);
 int queue_max_ctas_per_sm(int variant, int BE);
 
 // Batch in two launches (ef_assemble.cu): the element kernel over every

@@ -91,6 +91,7 @@ def load():
             "ef_plan_info": ([P, C.POINTER(PlanInfo)], I),
             "ef_plan_set_block": ([P, I, P], I),
             "ef_plan_set_pipeline": ([P, I, P], I),
+            "ef_plan_inject_stall": ([P, I, P], I),
             "ef_plan_tune": ([P, P, P, P, P, I, C.POINTER(C.c_int), P], I),
             "ef_plan_profile": ([P, I], I),
             "ef_plan_profile_read": ([P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)], I),
@@ -317,6 +318,11 @@ class Plan:
 
     def set_pipeline(self, chunks: int, stream=None):
         _check(load().ef_plan_set_pipeline(self.handle, int(chunks), _stream_ptr(stream)))
+
+    def inject_stall(self, on: bool, stream=None):
+        """Fault injection for tests: the queue's sums wait for a tile that never completes, give up after about
+        a second and the next check() raises EF_ERR_TIMEOUT; inject_stall(False) restores the schedule."""
+        _check(load().ef_plan_inject_stall(self.handle, int(bool(on)), _stream_ptr(stream)))
 
     def tune(self, nodes, coeff=None, K=None, M=None, reps: int = 5, stream=None) -> int:
         """Pick the fastest ef_assemble schedule for this plan: 0 (two-pass), chunks*100 + elem_ctas*10 + (tile

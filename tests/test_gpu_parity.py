@@ -265,6 +265,44 @@ def test_errors_are_reported():
     assert e.value.code == ef.EF_ERR_DEGENERATE
 
 
+def test_poisoned_queue_times_out_and_recovers():
+    """The one-launch queue's waits are bounded: with the first element
+    chunk's completion count raised from the host (a tile that never comes),
+    the sums give up after about a second, the call reports EF_ERR_TIMEOUT
+    and the GPU stays usable; with the count restored the queue gives the
+    two-pass bits again."""
+    import time
+
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(12, 0.2, 21)
+    coeff = mg.log_uniform_coeff(21, elems.shape[0])
+    plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).cuda())
+    tn, tc = torch.from_numpy(nodes).cuda(), torch.from_numpy(coeff).cuda()
+    K0, M0 = plan.assemble(tn, tc)
+    plan.check()
+    with pytest.raises(ef.EdgeFemError) as e:        # the two-pass schedule has no waits to poison
+        plan.inject_stall(True)
+    assert e.value.code == ef.EF_ERR_ARG
+    plan.set_pipeline(4)
+    plan.inject_stall(True)
+    t0 = time.perf_counter()
+    plan.assemble(tn, tc)
+    with pytest.raises(ef.EdgeFemError) as e:
+        plan.check()
+    elapsed = time.perf_counter() - t0
+    assert e.value.code == ef.EF_ERR_TIMEOUT
+    assert 0.5 < elapsed < 20.0, elapsed
+    plan.check()                                     # the status word was cleared
+    plan.inject_stall(False)
+    K1, M1 = plan.assemble(tn, tc)
+    plan.check()
+    assert torch.equal(K0, K1) and torch.equal(M0, M1)
+    plan.close()
+
+
 def test_cuda_graph_capture_replays_bitwise():
     """ef_assemble (one persistent launch with self-resetting queue counters)
     captured in a CUDA graph and replayed gives the same bits as a direct
