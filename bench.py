@@ -57,7 +57,7 @@ ADJOINT_FP64_OPS_PER_TET = 9 + 18 + 12 + 9 + 8 + 2 + 6 + 9 + 17 + 30 + 6 + 6 + 2
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
 # on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
 # to the elements.
-ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (110.016256e6 + 196.132096e6) / 663552
+ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (76.359936e6 + 166.353920e6) / 663552
 
 
 def _peaks():
