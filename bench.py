@@ -403,8 +403,46 @@ def run_adjoint(args, dev):
     return out
 
 
+ALL_CORES_CUBE = 48   # cubes per axis of each process's sample in the all-cores oracle run
+
+
+def _oracle_process(barrier, n):
+    """One process of the all-cores oracle run: its own n^3 sample of the
+    workload recipe, timed between a start aligned with the other processes
+    and its end (wall clock)."""
+    import oracle
+
+    nodes, elems = mg.kuhn_cube(n, WORKLOAD["jitter"], WORKLOAD["seed"])
+    coeff = mg.log_uniform_coeff(WORKLOAD["seed"], elems.shape[0])
+    oracle.assemble(WORKLOAD["kind"], WORKLOAD["dim"], *mg.kuhn_cube(2, 0.0, 0))   # load the library
+    barrier.wait()
+    t0 = time.time()
+    oracle.assemble(WORKLOAD["kind"], WORKLOAD["dim"], nodes, elems, coeff)
+    return elems.shape[0], t0, time.time()
+
+
+def _oracle_all_cores(cores):
+    """The oracle as it stands on every host core: `cores` independent
+    processes (spawned, so none inherits the parent's CUDA context), each
+    assembling its own sample; rate = all their elements / the time from the
+    common start to the last end."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as manager:
+        barrier = manager.Barrier(cores)
+        with ctx.Pool(cores) as pool:
+            res = pool.starmap(_oracle_process, [(barrier, ALL_CORES_CUBE)] * cores)
+    T = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": T / wall / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, each its own {ALL_CORES_CUBE}^3 x 6 tets ({res[0][0]} tets) of the "
+                      f"workload recipe, topology + pattern + quadrature assembly, {wall:.1f} s"}
+
+
 def cpu_baseline():
-    """The oracle as it stands, timed on this host: the full workload, one thread."""
+    """The oracle as it stands, timed on this host: the full workload, one
+    thread; and on every host core (independent processes, one sample each)."""
     import oracle
 
     oracle.build()
@@ -412,9 +450,16 @@ def cpu_baseline():
     t0 = time.perf_counter()
     oracle.assemble(WORKLOAD["kind"], WORKLOAD["dim"], nodes, elems, coeff)
     dt = time.perf_counter() - t0
-    return {"value": elems.shape[0] / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the full workload ({elems.shape[0]} tets), topology + pattern + quadrature assembly, "
-                      f"single thread, {dt:.1f} s"}
+    out = {"value": elems.shape[0] / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"the full workload ({elems.shape[0]} tets), topology + pattern + quadrature assembly, "
+                     f"single thread, {dt:.1f} s"}
+    cores = os.cpu_count() or 1
+    if cores > 1:
+        try:
+            out["all_cores"] = _oracle_all_cores(cores)
+        except Exception as exc:   # a host that cannot start the processes: report why
+            out["all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"}
+    return out
 
 
 def run_gpu(args):
