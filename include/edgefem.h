@@ -318,6 +318,17 @@ int ef_fe_curl(const ef_plan* plan, const double* d_nodes, const double* d_v, do
  * synchronises `stream`). Asynchronous afterwards. */
 int ef_load_vector(ef_plan* plan, const double* d_nodes, int n, const double* d_F, double* d_b, void* stream);
 
+/* Derivative load vector b_i = int_Omega g . D eta_i with D = div (RT0) or
+ * curl (Nedelec), as in the right-hand sides of the majorant minimisation
+ * (Sec. 4.1, int f div phi) and of curl-type sources; D eta_i is constant on
+ * an element (the values of ef_fe_curl's basis), so each element contributes
+ * s_i (|det B_K| sum_q w_q g(x_q)) . D phi_i. g given at the points of
+ * ef_quad_points: d_g [nq][n_elems][nc], nc = 3 for 3D Nedelec, 1 otherwise.
+ * Summed per DOF in ascending element order (bitwise reproducible), with the
+ * incidence and scratch of ef_load_vector (built on first use of either).
+ * Errors: EF_ERR_ARG, EF_ERR_OOM. */
+int ef_load_derivative(ef_plan* plan, const double* d_nodes, int n, const double* d_g, double* d_b, void* stream);
+
 /* ---- batched assembly of many meshes ---------------------------------------- */
 
 /*

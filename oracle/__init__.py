@@ -16,6 +16,9 @@ definition of the paper it follows. Functions:
 * ``local(kind, dim, P, sign, coeff)``: one element's K and M.
 * ``adjoint(kind, dim, nodes, elems, coeff, u, v)`` -> (J, dJ/dx, dJ/dsigma).
 * ``quadrature(dim, rule, n)`` and ``ref_basis(kind, dim, x)``.
+* Integration (Sec. 3.1): ``quad_points``, ``norm_l2``, ``fe_values``,
+  ``fe_curl`` (per-element curl or divergence), ``load_vector``
+  (int F . eta_i) and ``load_derivative`` (int g . D eta_i, D = div or curl).
 """
 from __future__ import annotations
 
@@ -103,6 +106,7 @@ def _load():
         lib.ora_quad_points.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P]
         lib.ora_norm_l2.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, C.c_int, P, P, P, P]
         lib.ora_load_vector.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P, P]
+        lib.ora_load_derivative.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P, P]
         lib.ora_fe_values.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, C.c_int, P, P]
         lib.ora_fe_curl.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P]
         lib.ora_adjoint.argtypes = [C.c_int, C.c_int, C.c_int64, P, C.c_int64, P, P, P, P, C.c_int, C.c_int,
@@ -234,6 +238,21 @@ def load_vector(kind: int, dim: int, nodes, elems, n: int, F):
     N = topology(kind, dim, nodes, elems)["n_dofs"]
     b = np.zeros(N)
     st = lib.ora_load_vector(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), n, _ptr(F), _ptr(b))
+    if st:
+        raise OracleError(st)
+    return b
+
+
+def load_derivative(kind: int, dim: int, nodes, elems, n: int, g):
+    """b_i = int g . D eta_i (D = div for RT0, curl for Nedelec), g: [nq, T, ncomp] at quad_points (ncomp 3 for
+    3D Nedelec, else 1; a [nq, T] array is taken as ncomp 1)."""
+    lib = _load()
+    nodes, elems, _ = _prep(nodes, elems, None)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    N = topology(kind, dim, nodes, elems)["n_dofs"]
+    b = np.zeros(N)
+    st = lib.ora_load_derivative(kind, dim, nodes.shape[0], _ptr(nodes), elems.shape[0], _ptr(elems), n, _ptr(g),
+                                 _ptr(b))
     if st:
         raise OracleError(st)
     return b

@@ -1050,6 +1050,61 @@ int ora_load_vector(int kind, int dim, int64_t V, const double* nodes, int64_t T
     return ORA_OK;
 }
 
+/* Derivative load vector b_i = int g . D eta_i with D = div (RT0) or curl
+ * (Nedelec), by the collapsed Gauss-Legendre rule (n per direction). The
+ * derivative of a mapped basis function is constant on an element and comes
+ * from the reference basis's derivatives: div eta_k / det B (Eq. RT0piola),
+ * curl eta_k / det B (2D) and B curl eta_k / det B (3D) (Ned0piola2/3).
+ * g: [q][element][ncomp] at ora_quad_points, ncomp = 3 for 3D Nedelec, 1
+ * otherwise. Element by element in ascending order: b[dof_k] += s_k |det B|
+ * sum_q w_q g_q . D eta_k. */
+int ora_load_derivative(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems, int n,
+                        const double* g, double* b)
+{
+    static qrule q;
+    ora_result topo;
+    if (!valid_kind(kind, dim)) return ORA_ERR_ARG;
+    int st = make_rule(dim, 1, n, &q);
+    if (st) return st;
+    st = ora_topology(kind, dim, V, nodes, T, elems, &topo);
+    if (st) return st;
+    const affine_field* basis = ref_basis(kind, dim);
+    int nl = nloc_of(kind, dim);
+    int nc = (kind == ORA_NED1 && dim == 3) ? 3 : 1;
+    for (int64_t i = 0; i < topo.n_dofs; i++) b[i] = 0.0;
+    for (int64_t e = 0; e < T; e++) {
+        double P[4][3], B[3][3], Bi[3][3], det;
+        st = element_frame(dim, nodes, elems + e * (dim + 1), P, B, Bi, &det);
+        if (st) {
+            ora_free(&topo);
+            return st;
+        }
+        for (int k = 0; k < nl; k++) {
+            const affine_field* f = &basis[k];
+            double D[3] = {0.0, 0.0, 0.0};
+            if (kind == ORA_RT0) {
+                for (int r = 0; r < dim; r++) D[0] += f->A[r][r];
+                D[0] /= det;
+            } else if (dim == 2) {
+                D[0] = (f->A[1][0] - f->A[0][1]) / det;
+            } else {
+                double cr[3] = {f->A[2][1] - f->A[1][2], f->A[0][2] - f->A[2][0], f->A[1][0] - f->A[0][1]};
+                for (int r = 0; r < 3; r++)
+                    for (int c = 0; c < 3; c++) D[r] += B[r][c] * cr[c] / det;
+            }
+            double acc = 0.0;
+            for (int i = 0; i < q.n; i++) {
+                double d = 0.0;
+                for (int c = 0; c < nc; c++) d += g[((int64_t)i * T + e) * nc + c] * D[c];
+                acc += q.w[i] * d;
+            }
+            b[topo.elem2dof[e * nl + k]] += topo.sign[e * nl + k] * fabs(det) * acc;
+        }
+    }
+    ora_free(&topo);
+    return ORA_OK;
+}
+
 /* Values at the points of ora_quad_points of v_h = sum_k s_k v[dof_k] phi_k:
  * out [q][element][dim]. */
 int ora_fe_values(int kind, int dim, int64_t V, const double* nodes, int64_t T, const int32_t* elems, int n,

@@ -461,6 +461,58 @@ __global__ void __launch_bounds__(ITPB) k_load_local(const int32_t* __restrict__
     }
 }
 
+// Local derivative load vectors l_k = s_k (|det B| sum_q w_q g(x_q)) . D phi_k
+// with D phi_k constant on the element (as in k_fe_curl): RT0 div phi_k =
+// dim / det B; 2D Nedelec curl phi_k = 2 / det B; 3D Nedelec curl phi_k =
+// 2 w_k / det B. g: [q][element][nc], nc = 3 for 3D Nedelec, else 1.
+template <int VAR>
+__global__ void __launch_bounds__(ITPB) k_load_deriv_local(const int32_t* __restrict__ elems,
+                                                           const double* __restrict__ nodes,
+                                                           const uint8_t* __restrict__ signbits,
+                                                           const double* __restrict__ gf, int64_t T, Rule1D r,
+                                                           double* __restrict__ local, int* status)
+{
+    constexpr int DIM = ElemTraits<VAR>::DIM;
+    constexpr int NL = ElemTraits<VAR>::NL;
+    constexpr int NC = VAR == NED3 ? 3 : 1;
+    __shared__ double table[QMAX][4];
+    const int nq = fill_rule_table<DIM>(r, table);
+    const int64_t e = (int64_t)blockIdx.x * ITPB + threadIdx.x;
+    if (e >= T) return;
+    double p[4][3], B[3][3];
+    load_vertices<DIM>(elems, nodes, e, p);
+    const double det = edge_frame<DIM>(p, B);
+    if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+    double gi[3] = {0.0, 0.0, 0.0};   // sum_q w_q g(x_q)
+    for (int q = 0; q < nq; q++) {
+        const double* gq = gf + ((int64_t)q * T + e) * NC;
+#pragma unroll
+        for (int c = 0; c < NC; c++) gi[c] = fma(table[q][3], __ldg(gq + c), gi[c]);
+    }
+    // |det B| / det B = sign(det B): the integral times the derivative's 1 / det B
+    const double f = (det < 0.0 ? -1.0 : 1.0) * (VAR == RT3 ? 3.0 : 2.0);
+    const uint32_t neg = __ldg(signbits + e);
+    double l[6];
+    if (VAR == NED3) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) l[k] = 0.0;
+#pragma unroll
+        for (int r2 = 0; r2 < 3; r2++) {
+            const double w[6] = {B[r2][2] - B[r2][1], B[r2][0] - B[r2][2], B[r2][1] - B[r2][0], B[r2][2], B[r2][0],
+                                 B[r2][1]};
+#pragma unroll
+            for (int k = 0; k < 6; k++) l[k] = fma(gi[r2], w[k], l[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) l[k] *= f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < NL; k++) l[k] = f * gi[0];
+    }
+#pragma unroll
+    for (int k = 0; k < NL; k++) local[e * NL + k] = ((neg >> k) & 1u) ? -l[k] : l[k];
+}
+
 // b[dof] = sum of its local entries in ascending element order (the DOF's
 // incidence segment: element * nl + k, sorted by DOF, stable in element).
 __global__ void __launch_bounds__(ITPB) k_load_sum(const uint32_t* __restrict__ off, const uint32_t* __restrict__ inc,
@@ -563,6 +615,75 @@ int make_rule(int dim, int n, Rule1D* r, int* nq)
 
 using namespace ef;
 
+namespace {
+
+// DOF -> (element, local DOF) incidence, ascending element order inside a
+// DOF, and the per-(element, local DOF) scratch of the load vectors; built on
+// first use (allocates, synchronises `s`).
+int ensure_load_incidence(ef_plan* plan, cudaStream_t s)
+{
+    if (plan->d_dof_inc) return EF_OK;
+    const int64_t nl = plan->nl, n_inc = plan->T * nl;
+    uint64_t* keys = nullptr;
+    uint32_t* cnt = nullptr;
+    void* tmp = nullptr;
+    size_t tb = radix_tmp_bytes(n_inc);
+    if (scan_tmp_bytes(plan->N) > tb) tb = scan_tmp_bytes(plan->N);
+    int st = EF_OK;
+    if (cudaMalloc((void**)&plan->d_dof_inc, n_inc * 4) != cudaSuccess ||
+        cudaMalloc((void**)&plan->d_dof_off, (plan->N + 1) * 4) != cudaSuccess ||
+        cudaMalloc((void**)&plan->d_load_local, n_inc * 8) != cudaSuccess ||
+        cudaMalloc((void**)&keys, n_inc * 8) != cudaSuccess || cudaMalloc((void**)&cnt, plan->N * 4) != cudaSuccess ||
+        cudaMalloc(&tmp, tb) != cudaSuccess) {
+        set_last_error("cudaMalloc(load vector)", cudaErrorMemoryAllocation);
+        st = EF_ERR_OOM;
+    }
+    if (st == EF_OK) {
+        cudaMemsetAsync(cnt, 0, plan->N * 4, s);
+        k_dof_keys<<<(unsigned)((n_inc + ITPB - 1) / ITPB), ITPB, 0, s>>>(plan->d_elem2dof, n_inc, keys,
+                                                                          plan->d_dof_inc, cnt);
+        st = radix_sort_pairs(keys, plan->d_dof_inc, n_inc, bits_for((uint64_t)plan->N), tmp, s);
+        if (st == EF_OK) st = exclusive_scan_u32(cnt, plan->d_dof_off, plan->N, true, tmp, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (st == EF_OK && e != cudaSuccess) {
+            set_last_error("load vector incidence", e);
+            st = EF_ERR_CUDA;
+        }
+    }
+    cudaFree(keys);
+    cudaFree(cnt);
+    cudaFree(tmp);
+    if (st != EF_OK) {
+        cudaFree(plan->d_dof_inc);
+        cudaFree(plan->d_dof_off);
+        cudaFree(plan->d_load_local);
+        plan->d_dof_inc = plan->d_dof_off = nullptr;
+        plan->d_load_local = nullptr;
+    }
+    return st;
+}
+
+// Shared argument checks of the load vectors; *done if there is nothing to
+// integrate (b zeroed).
+int load_checks(ef_plan* plan, const double* d_nodes, int n, const double* d_in, double* d_b, Rule1D* r,
+                cudaStream_t s, bool* done)
+{
+    *done = false;
+    if (!plan) return EF_ERR_ARG;
+    int nq = 0;
+    EF_TRY(make_rule(plan->dim, n, r, &nq));
+    if (plan->N > 0 && !d_b) return EF_ERR_ARG;
+    if (plan->T == 0) {
+        if (plan->N > 0) EF_CUDA(cudaMemsetAsync(d_b, 0, (size_t)plan->N * sizeof(double), s));
+        *done = true;
+        return EF_OK;
+    }
+    if (!d_nodes || !d_in) return EF_ERR_ARG;
+    return ensure_load_incidence(plan, s);
+}
+
+}  // namespace
+
 extern "C" {
 
 int ef_quad_rule(int dim, int n, double* h_xhat, double* h_w, int cap, int* nq)
@@ -653,60 +774,14 @@ int ef_fe_curl(const ef_plan* plan, const double* d_nodes, const double* d_v, do
     return EF_OK;
 }
 
+
 int ef_load_vector(ef_plan* plan, const double* d_nodes, int n, const double* d_F, double* d_b, void* stream)
 {
-    if (!plan) return EF_ERR_ARG;
-    Rule1D r;
-    int nq = 0;
-    EF_TRY(make_rule(plan->dim, n, &r, &nq));
     cudaStream_t s = (cudaStream_t)stream;
-    if (plan->N > 0 && !d_b) return EF_ERR_ARG;
-    if (plan->T == 0) {
-        if (plan->N > 0) EF_CUDA(cudaMemsetAsync(d_b, 0, (size_t)plan->N * sizeof(double), s));
-        return EF_OK;
-    }
-    if (!d_nodes || !d_F) return EF_ERR_ARG;
-    const int64_t nl = plan->nl, n_inc = plan->T * nl;
-    if (!plan->d_dof_inc) {
-        // DOF -> (element, local DOF) incidence, ascending element order inside a DOF
-        uint64_t* keys = nullptr;
-        uint32_t* cnt = nullptr;
-        void* tmp = nullptr;
-        size_t tb = radix_tmp_bytes(n_inc);
-        if (scan_tmp_bytes(plan->N) > tb) tb = scan_tmp_bytes(plan->N);
-        int st = EF_OK;
-        if (cudaMalloc((void**)&plan->d_dof_inc, n_inc * 4) != cudaSuccess ||
-            cudaMalloc((void**)&plan->d_dof_off, (plan->N + 1) * 4) != cudaSuccess ||
-            cudaMalloc((void**)&plan->d_load_local, n_inc * 8) != cudaSuccess ||
-            cudaMalloc((void**)&keys, n_inc * 8) != cudaSuccess || cudaMalloc((void**)&cnt, plan->N * 4) != cudaSuccess ||
-            cudaMalloc(&tmp, tb) != cudaSuccess) {
-            set_last_error("cudaMalloc(load vector)", cudaErrorMemoryAllocation);
-            st = EF_ERR_OOM;
-        }
-        if (st == EF_OK) {
-            cudaMemsetAsync(cnt, 0, plan->N * 4, s);
-            k_dof_keys<<<(unsigned)((n_inc + ITPB - 1) / ITPB), ITPB, 0, s>>>(plan->d_elem2dof, n_inc, keys,
-                                                                              plan->d_dof_inc, cnt);
-            st = radix_sort_pairs(keys, plan->d_dof_inc, n_inc, bits_for((uint64_t)plan->N), tmp, s);
-            if (st == EF_OK) st = exclusive_scan_u32(cnt, plan->d_dof_off, plan->N, true, tmp, s);
-            cudaError_t e = cudaStreamSynchronize(s);
-            if (st == EF_OK && e != cudaSuccess) {
-                set_last_error("ef_load_vector incidence", e);
-                st = EF_ERR_CUDA;
-            }
-        }
-        cudaFree(keys);
-        cudaFree(cnt);
-        cudaFree(tmp);
-        if (st != EF_OK) {
-            cudaFree(plan->d_dof_inc);
-            cudaFree(plan->d_dof_off);
-            cudaFree(plan->d_load_local);
-            plan->d_dof_inc = plan->d_dof_off = nullptr;
-            plan->d_load_local = nullptr;
-            return st;
-        }
-    }
+    Rule1D r;
+    bool done = false;
+    EF_TRY(load_checks(plan, d_nodes, n, d_F, d_b, &r, s, &done));
+    if (done) return EF_OK;
     const unsigned g = (unsigned)((plan->T + ITPB - 1) / ITPB);
     const uint8_t* sb = plan->d_signbits;
     double* loc = plan->d_load_local;
@@ -715,6 +790,28 @@ int ef_load_vector(ef_plan* plan, const double* d_nodes, int n, const double* d_
         case NED2: k_load_local<NED2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_F, plan->T, r, loc, plan->d_status); break;
         case RT3: k_load_local<RT3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_F, plan->T, r, loc, plan->d_status); break;
         default: k_load_local<NED3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_F, plan->T, r, loc, plan->d_status); break;
+    }
+    k_load_sum<<<(unsigned)((plan->N + ITPB - 1) / ITPB), ITPB, 0, s>>>(plan->d_dof_off, plan->d_dof_inc, loc, plan->N,
+                                                                         d_b);
+    EF_CUDA(cudaGetLastError());
+    return EF_OK;
+}
+
+int ef_load_derivative(ef_plan* plan, const double* d_nodes, int n, const double* d_g, double* d_b, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    Rule1D r;
+    bool done = false;
+    EF_TRY(load_checks(plan, d_nodes, n, d_g, d_b, &r, s, &done));
+    if (done) return EF_OK;
+    const unsigned g = (unsigned)((plan->T + ITPB - 1) / ITPB);
+    const uint8_t* sb = plan->d_signbits;
+    double* loc = plan->d_load_local;
+    switch (plan->variant) {
+        case RT2: k_load_deriv_local<RT2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_g, plan->T, r, loc, plan->d_status); break;
+        case NED2: k_load_deriv_local<NED2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_g, plan->T, r, loc, plan->d_status); break;
+        case RT3: k_load_deriv_local<RT3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_g, plan->T, r, loc, plan->d_status); break;
+        default: k_load_deriv_local<NED3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, sb, d_g, plan->T, r, loc, plan->d_status); break;
     }
     k_load_sum<<<(unsigned)((plan->N + ITPB - 1) / ITPB), ITPB, 0, s>>>(plan->d_dof_off, plan->d_dof_inc, loc, plan->N,
                                                                          d_b);

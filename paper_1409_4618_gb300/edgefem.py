@@ -123,6 +123,7 @@ def load():
             "ef_norm_l2": ([P, P, I, I, P, P, P, P, P], I),
             "ef_fe_curl": ([P, P, P, P, P], I),
             "ef_load_vector": ([P, P, I, P, P, P], I),
+            "ef_load_derivative": ([P, P, I, P, P, P], I),
             "ef_status_string": ([I], C.c_char_p),
             "ef_last_error": ([], C.c_char_p),
         }
@@ -410,6 +411,16 @@ class Plan:
         b = torch.empty(self.n_dofs, dtype=torch.float64, device=self.device)
         _check(load().ef_load_vector(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
                                      _dev(F, torch.float64, "F"), C.c_void_p(b.data_ptr()), _stream_ptr(stream)))
+        return b
+
+    def load_derivative(self, nodes, g, n: int, stream=None):
+        """b_i = int g . D eta_i (D = div for RT0, curl for Nedelec), g given at the quadrature points
+        [nq, n_elems, nc] (nc 3 for 3D Nedelec, else 1)."""
+        if not g.is_contiguous():
+            raise TypeError("g must be contiguous")
+        b = torch.empty(self.n_dofs, dtype=torch.float64, device=self.device)
+        _check(load().ef_load_derivative(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
+                                         _dev(g, torch.float64, "g"), C.c_void_p(b.data_ptr()), _stream_ptr(stream)))
         return b
 
     def norm_l2(self, nodes, f, n: int, v=None, per_element: bool = False, stream=None):

@@ -97,3 +97,36 @@ def test_load_vector_and_curl_parity(ora, kind, dim):
     assert np.array_equal(bg.view(np.uint64), b2.view(np.uint64))
     plan.check()
     plan.close()
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_load_derivative_parity(ora, kind, dim):
+    """ef_load_derivative (int g . D eta_i, D = div or curl) against the
+    oracle for a smooth g on a jittered mesh with shuffled local order; the
+    sums repeat bit for bit."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(7, 0.2, 53) if dim == 3 else mg.kuhn_square(19, 0.2, 53)
+    elems = mg.shuffle_local_order(elems, 153)
+    dev = torch.device("cuda")
+    tn = torch.from_numpy(nodes).to(dev)
+    plan = ef.Plan(kind, dim, nodes.shape[0], torch.from_numpy(elems).to(dev))
+    nc = 3 if (kind == NED1 and dim == 3) else 1
+    w = np.array([1.3, -0.7, 0.4])[:dim]
+    amp = np.array([0.9, -1.6, 0.5])[:nc]
+
+    def g(x):
+        return np.ascontiguousarray(np.sin(x @ w + 0.3)[..., None] * amp)
+
+    n = 3
+    xg = plan.quad_points(tn, n).cpu().numpy()
+    bg = plan.load_derivative(tn, torch.from_numpy(g(xg)).to(dev), n).cpu().numpy()
+    bo = ora.load_derivative(kind, dim, nodes, elems, n, g(ora.quad_points(dim, nodes, elems, n)))
+    assert np.max(np.abs(bo)) > 1e-3
+    assert np.max(np.abs(bg - bo)) <= 1e-12 * np.max(np.abs(bo))
+    b2 = plan.load_derivative(tn, torch.from_numpy(g(xg)).to(dev), n).cpu().numpy()
+    assert np.array_equal(bg.view(np.uint64), b2.view(np.uint64))
+    plan.check()
+    plan.close()

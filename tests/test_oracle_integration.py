@@ -172,3 +172,55 @@ def test_oracle_curl_of_interpolant_is_exact(ora, kind, dim):
     vals = ora.fe_values(kind, dim, nodes, elems, 2, u)
     x = ora.quad_points(dim, nodes, elems, 2)
     assert np.abs(vals - (x @ A.T + c)).max() < 2.0 * np.abs(A).sum() / 3
+
+
+def _bubble_and_gradient(x):
+    """b(x) = prod_i x_i (x_i - 1), which vanishes on the boundary of the unit
+    square / cube, and its gradient, at points x [..., dim]."""
+    a = x * (x - 1.0)
+    g = 2.0 * x - 1.0
+    dim = x.shape[-1]
+    b = np.prod(a, axis=-1)
+    grad = np.stack([g[..., i] * np.prod(np.delete(a, i, axis=-1), axis=-1) for i in range(dim)], -1)
+    return b, grad
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_oracle_derivative_load_vector_by_parts(ora, kind, dim):
+    """int g D eta_i for a g vanishing on the boundary equals, by integration
+    by parts, a plain load vector of derivatives of g: div (RT0):
+    int b div eta = -int grad b . eta; 2D curl: int b curl eta = int (d_y b,
+    -d_x b) . eta; 3D curl with G = b c: int G . curl eta = int (grad b x c) .
+    eta. The rule is exact for both sides (degree 2 dim + 1 <= 2n - dim)."""
+    nodes, elems = _mesh(dim, 3, 41)
+    n = 4 if dim == 2 else 5
+    x = ora.quad_points(dim, nodes, elems, n)
+    b, gb = _bubble_and_gradient(x)
+    if kind == RT0:
+        lhs = ora.load_derivative(kind, dim, nodes, elems, n, b[..., None])
+        rhs = -ora.load_vector(kind, dim, nodes, elems, n, gb)
+    elif dim == 2:
+        lhs = ora.load_derivative(kind, dim, nodes, elems, n, b[..., None])
+        rhs = ora.load_vector(kind, dim, nodes, elems, n, np.stack([gb[..., 1], -gb[..., 0]], -1))
+    else:
+        c = np.array([0.3, -1.1, 0.8])
+        lhs = ora.load_derivative(kind, dim, nodes, elems, n, b[..., None] * c)
+        rhs = ora.load_vector(kind, dim, nodes, elems, n, np.cross(gb, c))
+    assert np.max(np.abs(lhs)) > 1e-4
+    assert np.max(np.abs(lhs - rhs)) < 1e-13 * np.max(np.abs(lhs))
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_oracle_derivative_load_vector_is_stiffness_energy(ora, kind, dim):
+    """With g = D u_h (its per-element curl or divergence) the derivative load
+    vector is K u: b_i = int D u_h . D eta_i, K the pinned stiffness matrix
+    (unit coefficient)."""
+    nodes, elems = _mesh(dim, 3, 43)
+    r = ora.assemble(kind, dim, nodes, elems)
+    u = mg.normal(43, mg.STREAM_U, r["n_dofs"])
+    d = ora.fe_curl(kind, dim, nodes, elems, u).reshape(elems.shape[0], -1)
+    n = 2
+    g = np.broadcast_to(d, (n ** dim,) + d.shape).copy()
+    b = ora.load_derivative(kind, dim, nodes, elems, n, g)
+    Ku = to_dense(r, "K") @ u
+    assert np.max(np.abs(b - Ku)) < 1e-13 * np.max(np.abs(Ku))
