@@ -14,7 +14,8 @@ CUDA events the library records on the launching stream inside the timed
 region), the HBM fraction of the whole step, the clocks seen while timing,
 the CPU oracle timed on this host, and the other workloads: batched (256
 meshes), adjoint (96^3), RT0 (3D 128^3, 2D 32^2) and the vectorised
-integration (L2 error at 27 points per element).
+integration (L2 error at 27 points per element) and the library share of the
+majorant minimisation (Sec. 4.1) on the 33.5 M-triangle square.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -352,6 +353,94 @@ def run_integration(args, dev, peaks):
     return out
 
 
+def run_majorant(args, dev, peaks):
+    """The library's share of the majorant minimisation (Sec. 4.1, Algorithm 1)
+    on the unit square with 2 m^2 triangles (m = 4096: Table 3's largest mesh,
+    33,554,432 triangles), 16-point rule (n = 4): RT0 K and M, the load
+    vectors int grad v . phi (ef_load_vector) and int f div phi
+    (ef_load_derivative), the error ||grad(u - v)||^2, and for each of the 3
+    iterations Table 3 prints ||grad v - y||^2 (ef_norm_l2) and ||div y + f||^2
+    (ef_norm_l2_derivative). The host solves are not part of it; grad v (per
+    element) and y are seeded normal values drawn on the device (they do not
+    change the work),
+    f and grad u are the bubble problem's. Rate = elements / time of all these
+    calls (one step)."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    m = args.majorant_m
+    nodes, elems = mg.kuhn_square(m)
+    T, V = elems.shape[0], nodes.shape[0]
+    tn = torch.from_numpy(nodes).to(dev)
+    plan = ef.Plan(1, 2, V, torch.from_numpy(elems).to(dev))
+    del elems
+    n = 4
+    nq = n * n
+    x = plan.quad_points(tn, n)                                       # [nq, T, 2]
+    a = x * (x - 1.0)
+    mf = (2.0 * (a[..., 0] + a[..., 1])).unsqueeze(-1).contiguous()   # -f = 2 (x(x-1) + y(y-1))
+    gu = torch.stack([(2.0 * x[..., 0] - 1.0) * a[..., 1], (2.0 * x[..., 1] - 1.0) * a[..., 0]], -1)
+    del x, a
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    gvt = torch.randn((T, 2), generator=gen, dtype=torch.float64, device=dev)
+    gv = gvt.unsqueeze(0).expand(nq, T, 2).contiguous()
+    gerr = (gu - gv).contiguous()
+    del gu, gvt
+    f = (-mf).contiguous()
+    y = torch.randn(plan.n_dofs, generator=gen, dtype=torch.float64, device=dev)
+    K = torch.empty(plan.nnz, dtype=torch.float64, device=dev)
+    M = torch.empty_like(K)
+    iters = 3
+
+    def step():
+        plan.assemble(tn, None, K, M)
+        plan.load_vector(tn, gv, n)
+        plan.load_derivative(tn, f, n)
+        plan.norm_l2(tn, gerr, n)
+        for _ in range(iters):
+            plan.norm_l2(tn, gv, n, v=y)
+            plan.norm_l2_derivative(tn, mf, n, v=y)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        step()
+    plan.check()
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = args.majorant_steps
+    _nvtx(torch, "timed")
+    a0.record(stream)
+    for _ in range(steps):
+        step()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    _nvtx(torch, None)
+    plan.check()
+    ms = a0.elapsed_time(a1) / steps
+    # algorithmic bytes of one step: per element the values at the points each
+    # call reads (8 B per component and point), connectivity (12 B) and the
+    # gathered coordinates (16 V / T) per call; the CSR values K, M (16 nnz);
+    # the local load entries written and re-read and the load vectors written;
+    # DOF ids, signs and the gathered y of the norms with y
+    calls = 4 + 2 * iters
+    per_pts = nq * 8 * (2 + 1 + 2 + iters * (2 + 1))
+    alg = (per_pts + calls * 12) * T + calls * 16 * V + 16 * plan.nnz + 2 * (2 * 3 * 8 * T + 8 * plan.n_dofs) \
+        + 2 * iters * (12 + 1 + 3 * 8) * T
+    gbs = alg / (ms / 1e3) / 1e9
+    out = {"value": T / (ms / 1e3) / 1e6, "unit": UNIT, "workload": f"rt2d_square{m}_majorant_q16",
+           "elements": int(T), "dofs": int(plan.n_dofs), "iterations": iters, "ms_per_step": ms,
+           "calls_per_step": {"ef_assemble": 1, "ef_load_vector": 1, "ef_load_derivative": 1,
+                              "ef_norm_l2": 1 + iters, "ef_norm_l2_derivative": iters},
+           "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                   "algorithmic_bytes_per_step": int(alg), "bytes_per_elem": alg / T}}
+    plan.close()
+    del gv, gerr, mf, f, K, M
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_adjoint(args, dev):
     """Adjoint of u^T K u + v^T M v on the 96^3 Nedelec workload (5,308,416
     tets, seed 5), against plain ef_assemble on the same mesh."""
@@ -475,7 +564,8 @@ def run_gpu(args):
         dev = torch.device("cuda", local)
         peaks, _ = _peaks()
         legs = {"batched": lambda: run_batched(args, dev, float("nan")), "adjoint": lambda: run_adjoint(args, dev),
-                "rt0": lambda: run_rt0(args, dev, peaks), "integration": lambda: run_integration(args, dev, peaks)}
+                "rt0": lambda: run_rt0(args, dev, peaks), "integration": lambda: run_integration(args, dev, peaks),
+                "majorant": lambda: run_majorant(args, dev, peaks)}
         print(json.dumps({"leg": args.only, **legs[args.only]()}), flush=True)
         return 0
     dist = None
@@ -629,6 +719,8 @@ def run_gpu(args):
         line["rt0"] = run_rt0(args, dev, peaks)
     if not args.no_integration:
         line["integration"] = run_integration(args, dev, peaks)
+    if not args.no_majorant:
+        line["majorant"] = run_majorant(args, dev, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -649,11 +741,15 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rt0", action="store_true")
-    ap.add_argument("--only", choices=["batched", "adjoint", "rt0", "integration"],
+    ap.add_argument("--only", choices=["batched", "adjoint", "rt0", "integration", "majorant"],
                     help="run one of the other workloads by itself (profiling)")
     ap.add_argument("--adjoint-cube", type=int, default=96)
     ap.add_argument("--no-integration", action="store_true")
     ap.add_argument("--integration-steps", type=int, default=50)
+    ap.add_argument("--no-majorant", action="store_true")
+    ap.add_argument("--majorant-m", type=int, default=4096,
+                    help="squares per axis of the majorant workload (2 m^2 triangles)")
+    ap.add_argument("--majorant-steps", type=int, default=5)
     ap.add_argument("--rt0-steps", type=int, default=20)
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)

@@ -305,6 +305,16 @@ int ef_fe_values(const ef_plan* plan, const double* d_nodes, const double* d_v, 
 int ef_norm_l2(ef_plan* plan, const double* d_nodes, int n, int ncomp, const double* d_f, const double* d_v,
                double* d_elem, double* d_total, void* stream);
 
+/* Squared L2 norm of g - D v_h, D v_h the per-element curl (Nedelec) or
+ * divergence (RT0) of the FE function of d_v (omitted if d_v is NULL), as in
+ * ||div y + f|| of the majorant (Sec. 4.1) or the curl part of the H(curl)
+ * energy error (Sec. 4.2); g given at the points of ef_quad_points: d_g
+ * [nq][n_elems][nc], nc = 3 for 3D Nedelec, 1 otherwise. Per element
+ * (d_elem, may be NULL) and total (d_total, may be NULL; fixed order), as
+ * ef_norm_l2, whose scratch it shares. Errors: EF_ERR_ARG, EF_ERR_OOM. */
+int ef_norm_l2_derivative(ef_plan* plan, const double* d_nodes, int n, const double* d_g, const double* d_v,
+                          double* d_elem, double* d_total, void* stream);
+
 /* Per-element curl (Nedelec) or divergence (RT0) of the FE function with DOF
  * vector d_v, constant on each element: d_out [n_elems] (2D Nedelec, RT0) or
  * [n_elems x 3] (3D Nedelec). Asynchronous. */

@@ -355,43 +355,6 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2(const int32_t* __restrict__ el
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// Physical basis functions at a point: phi_k(x) for the element's local DOFs
-// (unsigned). Nedelec: l_t grad l_h - l_h grad l_t (local edge t -> h);
-// RT0: (x - P_a(k)) / det B. xh: reference point; G: grad lambda_0..dim;
-// p: vertices; B: edge frame.
-template <int VAR>
-__device__ __forceinline__ void basis_at(const double* xh, const double (&G)[4][3], const double (&p)[4][3],
-                                         const double (&B)[3][3], double rdet, double (&phi)[6][3])
-{
-    constexpr int DIM = ElemTraits<VAR>::DIM;
-    constexpr int NL = ElemTraits<VAR>::NL;
-    if (VAR == NED2 || VAR == NED3) {
-        const double l[4] = {1.0 - xh[0] - xh[1] - xh[2], xh[0], xh[1], xh[2]};
-#pragma unroll
-        for (int k = 0; k < NL; k++) {
-            const int t = DIM == 3 ? kEdge3[k][0] : kEdge2[k][0];
-            const int h = DIM == 3 ? kEdge3[k][1] : kEdge2[k][1];
-#pragma unroll
-            for (int r = 0; r < 3; r++) phi[k][r] = fma(l[t], G[h][r], -(l[h] * G[t][r]));
-        }
-    } else {
-        double x[3];
-#pragma unroll
-        for (int r = 0; r < 3; r++) {
-            double v = p[0][r];
-#pragma unroll
-            for (int i = 0; i < DIM; i++) v = fma(B[r][i], xh[i], v);
-            x[r] = v;
-        }
-#pragma unroll
-        for (int k = 0; k < NL; k++) {
-            const int a = DIM == 3 ? 3 - k : k;
-#pragma unroll
-            for (int r = 0; r < 3; r++) phi[k][r] = (x[r] - p[a][r]) * rdet;
-        }
-    }
-}
-
 // grad lambda_0 .. lambda_DIM: rows of B^-1 (cofactor columns / det).
 template <int DIM>
 __device__ __forceinline__ void barycentric_gradients(const double (&B)[3][3], double rdet, double (&G)[4][3])
@@ -415,7 +378,33 @@ __device__ __forceinline__ void barycentric_gradients(const double (&B)[3][3], d
     for (int r = 0; r < 3; r++) G[0][r] = -(G[1][r] + G[2][r] + G[3][r]);
 }
 
-// Local load vectors l_k = s_k |det B| sum_q w_q F(x_q) . phi_k(x_q), F: [q][element][dim].
+// The rule with each weight times the barycentric coordinates of its point:
+// table[q][a] = w_q lambda_a(xhat_q), a = 0..DIM.
+template <int DIM>
+__device__ __forceinline__ int fill_lambda_table(const Rule1D& r, double (*table)[4])
+{
+    const int nq = DIM == 3 ? r.n * r.n * r.n : r.n * r.n;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        double xh[3];
+        const double w = quad_point<DIM>(r, q, xh);
+        table[q][0] = w * (1.0 - xh[0] - xh[1] - xh[2]);
+        table[q][1] = w * xh[0];
+        table[q][2] = w * xh[1];
+        table[q][3] = w * xh[2];
+    }
+    __syncthreads();
+    return nq;
+}
+
+// Local load vectors l_k = s_k |det B| sum_q w_q F(x_q) . phi_k(x_q), F:
+// [q][element][dim]. Every lowest-order basis function is affine, a
+// combination of the barycentric coordinates, so the rule is applied once
+// to the moments m_a = sum_q w_q lambda_a(x_q) F(x_q) (a = 0..dim; dim + 1
+// FMAs per point and component) and each l_k follows from them:
+//   Nedelec, edge t -> h: phi = lambda_t grad lambda_h - lambda_h grad lambda_t,
+//     sum_q w_q F . phi = grad lambda_h . m_t - grad lambda_t . m_h;
+//   RT0, opposite vertex a: phi = (x - P_a) / det B = sum_b lambda_b (P_b - P_a) / det B,
+//     sum_q w_q F . phi = sum_b (P_b - P_a) . m_b / det B.
 template <int VAR>
 __global__ void __launch_bounds__(ITPB) k_load_local(const int32_t* __restrict__ elems,
                                                      const double* __restrict__ nodes,
@@ -426,37 +415,60 @@ __global__ void __launch_bounds__(ITPB) k_load_local(const int32_t* __restrict__
     constexpr int DIM = ElemTraits<VAR>::DIM;
     constexpr int NL = ElemTraits<VAR>::NL;
     __shared__ double table[QMAX][4];
-    const int nq = fill_rule_table<DIM>(r, table);
+    const int nq = fill_lambda_table<DIM>(r, table);
     const int64_t e = (int64_t)blockIdx.x * ITPB + threadIdx.x;
     if (e >= T) return;
-    double p[4][3], B[3][3], G[4][3];
+    double p[4][3], B[3][3];
     load_vertices<DIM>(elems, nodes, e, p);
     const double det = edge_frame<DIM>(p, B);
     if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
     const double rdet = 1.0 / det;
-    barycentric_gradients<DIM>(B, rdet, G);
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double m[DIM + 1][DIM];
+#pragma unroll
+    for (int a = 0; a <= DIM; a++)
+#pragma unroll
+        for (int c = 0; c < DIM; c++) m[a][c] = 0.0;
     for (int q = 0; q < nq; q++) {
-        double phi[6][3];
-        basis_at<VAR>(table[q], G, p, B, rdet, phi);
         const double* fq = F + ((int64_t)q * T + e) * DIM;
-        double f[3] = {0.0, 0.0, 0.0};
+        double f[DIM];
 #pragma unroll
         for (int c = 0; c < DIM; c++) f[c] = __ldg(fq + c);
-        const double wq = table[q][3];
+#pragma unroll
+        for (int a = 0; a <= DIM; a++)
+#pragma unroll
+            for (int c = 0; c < DIM; c++) m[a][c] = fma(table[q][a], f[c], m[a][c]);
+    }
+    double l[NL];
+    if (VAR == NED2 || VAR == NED3) {
+        double G[4][3];
+        barycentric_gradients<DIM>(B, rdet, G);
 #pragma unroll
         for (int k = 0; k < NL; k++) {
+            const int t = DIM == 3 ? kEdge3[k][0] : kEdge2[k][0];
+            const int h = DIM == 3 ? kEdge3[k][1] : kEdge2[k][1];
             double d = 0.0;
 #pragma unroll
-            for (int c = 0; c < DIM; c++) d = fma(f[c], phi[k][c], d);
-            acc[k] = fma(wq, d, acc[k]);
+            for (int c = 0; c < DIM; c++) d = fma(G[h][c], m[t][c], fma(-G[t][c], m[h][c], d));
+            l[k] = d;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NL; k++) {
+            const int a = DIM == 3 ? 3 - k : k;
+            double d = 0.0;
+#pragma unroll
+            for (int b = 0; b <= DIM; b++)
+                if (b != a)
+#pragma unroll
+                    for (int c = 0; c < DIM; c++) d = fma(p[b][c] - p[a][c], m[b][c], d);
+            l[k] = d * rdet;
         }
     }
     const uint32_t neg = __ldg(signbits + e);
     const double adet = fabs(det);
 #pragma unroll
     for (int k = 0; k < NL; k++) {
-        const double v = adet * acc[k];
+        const double v = adet * l[k];
         local[e * NL + k] = ((neg >> k) & 1u) ? -v : v;
     }
 }
@@ -538,12 +550,44 @@ __global__ void k_dof_keys(const int32_t* __restrict__ e2d, int64_t n, uint64_t*
     atomicAdd(&cnt[d], 1u);
 }
 
-// Per element, the constant curl of the Nedelec function of v, with
+// The constant curl of the Nedelec function of v on an element, with
 // c_k = s_k v[dof_k] (Ned0piola3, curl phi_k = B curl eta_k / det B):
 //   2D: 2 / det B * sum_k c_k (every reference curl is 2);
 //   3D: 2 / det B * sum_k c_k w_k, w = (e3 - e2, e1 - e3, e2 - e1, e3, e1, e2)
 //   (B curl eta_k = 2 w_k, e_i the columns of B);
 // or the constant divergence of the RT0 function, dim / det B * sum_k c_k.
+// out[0] (2D, RT0) or out[0..2] (3D Nedelec).
+template <int VAR>
+__device__ __forceinline__ void fe_derivative(const double (&B)[3][3], double rdet, const int32_t* __restrict__ e2d,
+                                              uint32_t neg, const double* __restrict__ v, int64_t e,
+                                              double (&out)[3])
+{
+    constexpr int NL = ElemTraits<VAR>::NL;
+    double c[6];
+#pragma unroll
+    for (int k = 0; k < NL; k++) {
+        const double x = __ldg(v + __ldg(e2d + e * NL + k));
+        c[k] = ((neg >> k) & 1u) ? -x : x;
+    }
+    if (VAR == NED3) {
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            const double w[6] = {B[r][2] - B[r][1], B[r][0] - B[r][2], B[r][1] - B[r][0], B[r][2], B[r][0], B[r][1]};
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 6; k++) s = fma(c[k], w[k], s);
+            out[r] = 2.0 * s * rdet;
+        }
+    } else {
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < NL; k++) sum += c[k];
+        out[0] = (VAR == RT3 ? 3.0 : 2.0) * sum * rdet;
+        out[1] = out[2] = 0.0;
+    }
+}
+
+// Per element, the constant curl or divergence of the FE function of v.
 template <int VAR>
 __global__ void __launch_bounds__(ITPB) k_fe_curl(const int32_t* __restrict__ elems,
                                                   const double* __restrict__ nodes,
@@ -553,38 +597,69 @@ __global__ void __launch_bounds__(ITPB) k_fe_curl(const int32_t* __restrict__ el
                                                   double* __restrict__ out, int* status)
 {
     constexpr int DIM = ElemTraits<VAR>::DIM;
-    constexpr int NL = ElemTraits<VAR>::NL;
     const int64_t e = (int64_t)blockIdx.x * ITPB + threadIdx.x;
     if (e >= T) return;
     double p[4][3], B[3][3];
     load_vertices<DIM>(elems, nodes, e, p);
     const double det = edge_frame<DIM>(p, B);
     if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
-    const double rdet = 1.0 / det;
-    const uint32_t neg = __ldg(signbits + e);
-    double c[6];
-#pragma unroll
-    for (int k = 0; k < NL; k++) {
-        const double x = __ldg(v + __ldg(e2d + e * NL + k));
-        c[k] = ((neg >> k) & 1u) ? -x : x;
-    }
+    double d[3];
+    fe_derivative<VAR>(B, 1.0 / det, e2d, __ldg(signbits + e), v, e, d);
     if (VAR == NED3) {
-        // B curl eta_k = 2 w_k, w = (e3 - e2, e1 - e3, e2 - e1, e3, e1, e2): curl phi_k = 2 w_k / det B
-        double s[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-        for (int r = 0; r < 3; r++) {
-            const double w[6] = {B[r][2] - B[r][1], B[r][0] - B[r][2], B[r][1] - B[r][0], B[r][2], B[r][0], B[r][1]};
-#pragma unroll
-            for (int k = 0; k < 6; k++) s[r] = fma(c[k], w[k], s[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < 3; r++) out[e * 3 + r] = 2.0 * s[r] * rdet;
+        for (int r = 0; r < 3; r++) out[e * 3 + r] = d[r];
     } else {
-        double sum = 0.0;
-#pragma unroll
-        for (int k = 0; k < NL; k++) sum += c[k];
-        out[e] = (VAR == RT3 ? 3.0 : 2.0) * sum * rdet;
+        out[e] = d[0];
     }
+}
+
+// Per element: |det B| sum_q w_q |g_q - D v_h|^2, D v_h the constant curl or
+// divergence of the FE function of v (omitted when v is NULL); g:
+// [q][element][nc], nc = 3 for 3D Nedelec, else 1. CTA sums in a fixed tree.
+template <int VAR>
+__global__ void __launch_bounds__(ITPB) k_norm_l2_deriv(const int32_t* __restrict__ elems,
+                                                        const double* __restrict__ nodes,
+                                                        const int32_t* __restrict__ e2d,
+                                                        const uint8_t* __restrict__ signbits,
+                                                        const double* __restrict__ v, const double* __restrict__ g,
+                                                        int64_t T, Rule1D r, double* __restrict__ elem_out,
+                                                        double* __restrict__ part, int* status)
+{
+    constexpr int DIM = ElemTraits<VAR>::DIM;
+    constexpr int NC = VAR == NED3 ? 3 : 1;
+    __shared__ double table[QMAX][4];
+    __shared__ double red[ITPB];
+    const int nq = fill_rule_table<DIM>(r, table);
+    const int64_t e = (int64_t)blockIdx.x * ITPB + threadIdx.x;
+    double acc = 0.0;
+    if (e < T) {
+        double p[4][3], B[3][3];
+        load_vertices<DIM>(elems, nodes, e, p);
+        const double det = edge_frame<DIM>(p, B);
+        if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+        double d[3] = {0.0, 0.0, 0.0};
+        if (v) fe_derivative<VAR>(B, 1.0 / det, e2d, __ldg(signbits + e), v, e, d);
+        double s = 0.0;
+        for (int q = 0; q < nq; q++) {
+            const double* gq = g + ((int64_t)q * T + e) * NC;
+            double d2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const double x = __ldg(gq + c) - d[c];
+                d2 = fma(x, x, d2);
+            }
+            s = fma(table[q][3], d2, s);
+        }
+        acc = fabs(det) * s;
+        if (elem_out) elem_out[e] = acc;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = ITPB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 // The partial sums in one fixed order: thread t adds t, t + 1024, ..., then a tree.
@@ -850,6 +925,42 @@ int ef_norm_l2(ef_plan* plan, const double* d_nodes, int n, int ncomp, const dou
         case NED2: k_norm_l2<NED2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, d_f, ncomp, plan->T, r, d_elem, part, plan->d_status); break;
         case RT3: k_norm_l2<RT3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, d_f, ncomp, plan->T, r, d_elem, part, plan->d_status); break;
         default: k_norm_l2<NED3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, d_f, ncomp, plan->T, r, d_elem, part, plan->d_status); break;
+    }
+    if (d_total) k_sum_partials<<<1, 1024, 0, s>>>(part, nb, d_total);
+    EF_CUDA(cudaGetLastError());
+    return EF_OK;
+}
+
+int ef_norm_l2_derivative(ef_plan* plan, const double* d_nodes, int n, const double* d_g, const double* d_v,
+                          double* d_elem, double* d_total, void* stream)
+{
+    if (!plan) return EF_ERR_ARG;
+    Rule1D r;
+    int nq = 0;
+    EF_TRY(make_rule(plan->dim, n, &r, &nq));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->T == 0) {
+        if (d_total) EF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(double), s));
+        return EF_OK;
+    }
+    if (!d_nodes || !d_g) return EF_ERR_ARG;
+    const int64_t nb = (plan->T + ITPB - 1) / ITPB;
+    if (!plan->d_l2_part) {
+        cudaError_t e = cudaMalloc((void**)&plan->d_l2_part, (size_t)nb * sizeof(double));
+        if (e != cudaSuccess) {
+            set_last_error("cudaMalloc(l2 partials)", e);
+            return EF_ERR_OOM;
+        }
+    }
+    const unsigned g = (unsigned)nb;
+    const int32_t* e2d = plan->d_elem2dof;
+    const uint8_t* sb = plan->d_signbits;
+    double* part = plan->d_l2_part;
+    switch (plan->variant) {
+        case RT2: k_norm_l2_deriv<RT2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, d_g, plan->T, r, d_elem, part, plan->d_status); break;
+        case NED2: k_norm_l2_deriv<NED2><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, d_g, plan->T, r, d_elem, part, plan->d_status); break;
+        case RT3: k_norm_l2_deriv<RT3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, d_g, plan->T, r, d_elem, part, plan->d_status); break;
+        default: k_norm_l2_deriv<NED3><<<g, ITPB, 0, s>>>(plan->d_elems, d_nodes, e2d, sb, d_v, d_g, plan->T, r, d_elem, part, plan->d_status); break;
     }
     if (d_total) k_sum_partials<<<1, 1024, 0, s>>>(part, nb, d_total);
     EF_CUDA(cudaGetLastError());

@@ -122,6 +122,7 @@ def load():
             "ef_fe_values": ([P, P, P, I, P, P], I),
             "ef_norm_l2": ([P, P, I, I, P, P, P, P, P], I),
             "ef_fe_curl": ([P, P, P, P, P], I),
+            "ef_norm_l2_derivative": ([P, P, I, P, P, P, P, P], I),
             "ef_load_vector": ([P, P, I, P, P, P], I),
             "ef_load_derivative": ([P, P, I, P, P, P], I),
             "ef_status_string": ([I], C.c_char_p),
@@ -395,6 +396,20 @@ class Plan:
         _check(load().ef_fe_values(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(v, torch.float64, "v"),
                                    int(n), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
+
+    def norm_l2_derivative(self, nodes, g, n: int, v=None, per_element: bool = False, stream=None):
+        """Squared L2 norm of g - D v_h (D = div for RT0, curl for Nedelec; D v_h omitted without v), g given at
+        the quadrature points [nq, n_elems, nc] (nc 3 for 3D Nedelec, else 1): (total [1], per-element or None)."""
+        nc = 3 if (self.kind == EF_NED1 and self.dim == 3) else 1
+        if not g.is_contiguous() or g.dim() != 3 or g.shape[2] != nc:
+            raise TypeError(f"g must be a contiguous [nq, n_elems, {nc}] tensor")
+        total = torch.empty(1, dtype=torch.float64, device=self.device)
+        elem = torch.empty(self.n_elems, dtype=torch.float64, device=self.device) if per_element else None
+        _check(load().ef_norm_l2_derivative(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
+                                            _dev(g, torch.float64, "g"), _dev(v, torch.float64, "v"),
+                                            None if elem is None else C.c_void_p(elem.data_ptr()),
+                                            C.c_void_p(total.data_ptr()), _stream_ptr(stream)))
+        return total, elem
 
     def fe_curl(self, nodes, v, stream=None):
         """Per-element curl (Nedelec: [n_elems] in 2D, [n_elems, 3] in 3D) or divergence (RT0: [n_elems])."""

@@ -16,8 +16,8 @@ The majorant of Eq. (majorantestimate) squared by Young's inequality is
     M = (1 + 1/beta) ||grad v - y||^2 + (1 + beta) C^2 ||div y + f||^2,
 
 and I_eff = sqrt(M) / ||grad (u - v)||. The RT0 matrices, the two load
-vectors, div y and the three norms come from a backend: the oracle or the
-GPU library. The linear systems are solved by scipy (neither has a solver).
+vectors and the three norms (one of them of div y + f) come from a backend:
+the oracle or the GPU library. The linear systems are solved by scipy (neither has a solver).
 """
 from __future__ import annotations
 
@@ -95,8 +95,7 @@ def minimise(backend, nodes, elems, iters, n=4):
         rhs = -(1.0 + beta) * C * C * b_div + (1.0 + 1.0 / beta) * b_grad
         y = spla.spsolve(A.tocsc(), rhs)
         t1 = backend.norm_l2(gv, n, y)                             # ||grad v - y||^2
-        r = backend.div(y)[None, :] + fx
-        t2 = backend.norm_l2(np.ascontiguousarray(r[..., None]), n)   # ||div y + f||^2
+        t2 = backend.norm_derivative(np.ascontiguousarray(-fx[..., None]), n, y)   # ||div y + f||^2
         Mv = (1.0 + 1.0 / beta) * t1 + (1.0 + beta) * C * C * t2
         out.append((beta, math.sqrt(Mv), math.sqrt(Mv / err_v)))
         beta = math.sqrt(t1) / (C * math.sqrt(t2))
@@ -132,8 +131,10 @@ class OracleBackend:
     def norm_l2(self, f, n, v=None):
         return self.ora.norm_l2(RT0, self.dim, self.nodes, self.elems, n, f, v)[0]
 
-    def div(self, y):
-        return self.ora.fe_curl(RT0, self.dim, self.nodes, self.elems, y)
+    def norm_derivative(self, g, n, v):
+        """||g - div v_h||^2: the oracle's per-element divergence and norm."""
+        d = self.ora.fe_curl(RT0, self.dim, self.nodes, self.elems, v)
+        return self.norm_l2(np.ascontiguousarray(g - d[None, :, None]), n)
 
 
 class GpuBackend:
@@ -178,8 +179,9 @@ class GpuBackend:
         total, _ = self.plan.norm_l2(self.tn, self._t(f), n, None if v is None else self._t(v))
         return float(total[0])
 
-    def div(self, y):
-        return self.plan.fe_curl(self.tn, self._t(y)).cpu().numpy()
+    def norm_derivative(self, g, n, v):
+        total, _ = self.plan.norm_l2_derivative(self.tn, self._t(g), n, self._t(v))
+        return float(total[0])
 
     def close(self):
         self.plan.check()

@@ -43,9 +43,7 @@ def eddy_error_gpu(m, n=6):
     v = torch.from_numpy(spla.spsolve(A.tocsc(), b.cpu().numpy())).to(dev)
     E1, E2, curlE = exact(x[..., 0], x[..., 1], inside)
     l2, _ = plan.norm_l2(tn, torch.from_numpy(np.ascontiguousarray(np.stack([E1, E2], -1))).to(dev), n, v=v)
-    cv = plan.fe_curl(tn, v).cpu().numpy()
-    dc = torch.from_numpy(np.ascontiguousarray((curlE - cv[None, :])[..., None])).to(dev)
-    c2, _ = plan.norm_l2(tn, dc, n)
+    c2, _ = plan.norm_l2_derivative(tn, torch.from_numpy(np.ascontiguousarray(curlE[..., None])).to(dev), n, v=v)
     plan.check()
     plan.close()
     return N, float(np.sqrt(float(l2) + float(c2)))
@@ -128,5 +126,41 @@ def test_load_derivative_parity(ora, kind, dim):
     assert np.max(np.abs(bg - bo)) <= 1e-12 * np.max(np.abs(bo))
     b2 = plan.load_derivative(tn, torch.from_numpy(g(xg)).to(dev), n).cpu().numpy()
     assert np.array_equal(bg.view(np.uint64), b2.view(np.uint64))
+    plan.check()
+    plan.close()
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_norm_of_derivative_parity(ora, kind, dim):
+    """ef_norm_l2_derivative (||g - D v_h||^2, D = div or curl) against the
+    oracle's per-element derivative and norm, per element and in total; with
+    g = D v_h it vanishes."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(6, 0.2, 59) if dim == 3 else mg.kuhn_square(17, 0.2, 59)
+    elems = mg.shuffle_local_order(elems, 159)
+    dev = torch.device("cuda")
+    tn = torch.from_numpy(nodes).to(dev)
+    plan = ef.Plan(kind, dim, nodes.shape[0], torch.from_numpy(elems).to(dev))
+    nc = 3 if (kind == NED1 and dim == 3) else 1
+    n = 3
+    w = np.array([0.8, 1.7, -0.6])[:dim]
+    amp = np.array([1.2, 0.3, -0.9])[:nc]
+    xg = plan.quad_points(tn, n).cpu().numpy()
+    g = np.ascontiguousarray(np.cos(xg @ w)[..., None] * amp)
+    v = mg.normal(59, mg.STREAM_V, plan.n_dofs)
+    tot, per = plan.norm_l2_derivative(tn, torch.from_numpy(g).to(dev), n, v=torch.from_numpy(v).to(dev),
+                                       per_element=True)
+    d = ora.fe_curl(kind, dim, nodes, elems, v).reshape(elems.shape[0], nc)
+    xo = ora.quad_points(dim, nodes, elems, n)
+    go = np.cos(xo @ w)[..., None] * amp
+    to, po = ora.norm_l2(kind, dim, nodes, elems, n, go - d[None])
+    assert abs(float(tot[0]) - to) <= 1e-12 * to
+    assert np.max(np.abs(per.cpu().numpy() - po)) <= 1e-12 * np.max(po)
+    dg = plan.fe_curl(tn, torch.from_numpy(v).to(dev)).reshape(1, -1, nc).expand(n ** dim, -1, -1).contiguous()
+    zero, _ = plan.norm_l2_derivative(tn, dg, n, v=torch.from_numpy(v).to(dev))
+    assert float(zero[0]) <= 1e-24 * to
     plan.check()
     plan.close()

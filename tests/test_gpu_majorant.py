@@ -1,7 +1,8 @@
 """Table 3 (Sec. 4.1, majorant minimisation by Algorithm 1) through the
 library: RT0 2D matrices (ef_assemble), quadrature points, the load vectors
 int grad v . phi (ef_load_vector) and int f div phi (ef_load_derivative),
-div y (ef_fe_curl) and the three norms (ef_norm_l2) on the GPU; the P1
+and the three norms (ef_norm_l2; ef_norm_l2_derivative for div y + f) on
+the GPU; the P1
 approximation and the linear solves by scipy in the test. Every printed
 iterate of the 512- and 131,072-triangle meshes to the printed digits."""
 import pytest
