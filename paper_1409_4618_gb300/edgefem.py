@@ -305,6 +305,24 @@ class Plan:
             raise ValueError("plan is closed")
         return self._h
 
+    # The C ABI takes plain pointers and cannot see buffer sizes; the binding
+    # knows the plan's and rejects a wrong-sized tensor before the library
+    # would read or write past its end.
+    def _need(self, t, numel: int, name: str):
+        if t is not None and isinstance(t, torch.Tensor) and t.numel() != numel:
+            raise ValueError(f"{name} has {t.numel()} entries; this plan needs {numel}")
+
+    def _need_mesh(self, nodes, coeff=None, K=None, M=None, coeff_name="coeff"):
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        self._need(coeff, self.n_elems, coeff_name)
+        self._need(K, self.nnz, "K")
+        self._need(M, self.nnz, "M")
+
+    def _need_points(self, t, n: int, ncomp: int, name: str):
+        shape = (int(n) ** self.dim, self.n_elems, ncomp)
+        if not isinstance(t, torch.Tensor) or tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape} (points, elements, components)")
+
     def info(self) -> dict:
         return ef_plan_info(self.handle)
 
@@ -329,6 +347,7 @@ class Plan:
     def tune(self, nodes, coeff=None, K=None, M=None, reps: int = 5, stream=None) -> int:
         """Pick the fastest ef_assemble schedule for this plan: 0 (two-pass), chunks*100 + elem_ctas*10 + (tile
         == 256) (persistent queue) or -block (element-block path)."""
+        self._need_mesh(nodes, coeff, K, M)
         K, M = self._vals(K, M)
         chosen = C.c_int(0)
         _check(load().ef_plan_tune(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(coeff, torch.float64, "coeff"),
@@ -358,22 +377,27 @@ class Plan:
         return K, M
 
     def assemble(self, nodes, coeff=None, K=None, M=None, stream=None):
+        self._need_mesh(nodes, coeff, K, M)
         K, M = self._vals(K, M)
         ef_assemble(self.handle, nodes, coeff, K, M, stream)
         return K, M
 
     def assemble_two_pass(self, nodes, coeff=None, K=None, M=None, stream=None):
+        self._need_mesh(nodes, coeff, K, M)
         K, M = self._vals(K, M)
         ef_assemble_two_pass(self.handle, nodes, coeff, K, M, stream)
         return K, M
 
     def assemble2(self, nodes, coeff_K=None, coeff_M=None, K=None, M=None, stream=None):
         """K weighted by coeff_K, M by coeff_M (e.g. 1/mu and kappa)."""
+        self._need_mesh(nodes, coeff_K, K, M, "coeff_K")
+        self._need(coeff_M, self.n_elems, "coeff_M")
         K, M = self._vals(K, M)
         ef_assemble2(self.handle, nodes, coeff_K, coeff_M, K, M, stream)
         return K, M
 
     def assemble_host(self, nodes, coeff=None, K=None, M=None, stream=None):
+        self._need_mesh(nodes, coeff, K, M)
         if K is None:
             K = torch.empty(self.nnz, dtype=torch.float64, pin_memory=True)
         if M is None:
@@ -383,6 +407,7 @@ class Plan:
 
     def quad_points(self, nodes, n: int, stream=None):
         """Physical quadrature points [nq, n_elems, dim] (point-major)."""
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
         nq = n ** self.dim
         x = torch.empty((nq, self.n_elems, self.dim), dtype=torch.float64, device=self.device)
         _check(load().ef_quad_points(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
@@ -391,6 +416,8 @@ class Plan:
 
     def fe_values(self, nodes, v, n: int, stream=None):
         """Values [nq, n_elems, dim] of the FE function with DOF vector v at the quadrature points."""
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        self._need(v, self.n_dofs, "v")
         nq = n ** self.dim
         out = torch.empty((nq, self.n_elems, self.dim), dtype=torch.float64, device=self.device)
         _check(load().ef_fe_values(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(v, torch.float64, "v"),
@@ -401,8 +428,9 @@ class Plan:
         """Squared L2 norm of g - D v_h (D = div for RT0, curl for Nedelec; D v_h omitted without v), g given at
         the quadrature points [nq, n_elems, nc] (nc 3 for 3D Nedelec, else 1): (total [1], per-element or None)."""
         nc = 3 if (self.kind == EF_NED1 and self.dim == 3) else 1
-        if not g.is_contiguous() or g.dim() != 3 or g.shape[2] != nc:
-            raise TypeError(f"g must be a contiguous [nq, n_elems, {nc}] tensor")
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        self._need_points(g, n, nc, "g")
+        self._need(v, self.n_dofs, "v")
         total = torch.empty(1, dtype=torch.float64, device=self.device)
         elem = torch.empty(self.n_elems, dtype=torch.float64, device=self.device) if per_element else None
         _check(load().ef_norm_l2_derivative(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
@@ -413,6 +441,8 @@ class Plan:
 
     def fe_curl(self, nodes, v, stream=None):
         """Per-element curl (Nedelec: [n_elems] in 2D, [n_elems, 3] in 3D) or divergence (RT0: [n_elems])."""
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        self._need(v, self.n_dofs, "v")
         shape = (self.n_elems, 3) if (self.kind == EF_NED1 and self.dim == 3) else (self.n_elems,)
         out = torch.empty(shape, dtype=torch.float64, device=self.device)
         _check(load().ef_fe_curl(self.handle, _dev(nodes, torch.float64, "nodes"), _dev(v, torch.float64, "v"),
@@ -421,8 +451,8 @@ class Plan:
 
     def load_vector(self, nodes, F, n: int, stream=None):
         """b_i = int F . eta_i, F given at the quadrature points [nq, n_elems, dim]."""
-        if not F.is_contiguous():
-            raise TypeError("F must be contiguous")
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        self._need_points(F, n, self.dim, "F")
         b = torch.empty(self.n_dofs, dtype=torch.float64, device=self.device)
         _check(load().ef_load_vector(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
                                      _dev(F, torch.float64, "F"), C.c_void_p(b.data_ptr()), _stream_ptr(stream)))
@@ -431,8 +461,8 @@ class Plan:
     def load_derivative(self, nodes, g, n: int, stream=None):
         """b_i = int g . D eta_i (D = div for RT0, curl for Nedelec), g given at the quadrature points
         [nq, n_elems, nc] (nc 3 for 3D Nedelec, else 1)."""
-        if not g.is_contiguous():
-            raise TypeError("g must be contiguous")
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        self._need_points(g, n, 3 if (self.kind == EF_NED1 and self.dim == 3) else 1, "g")
         b = torch.empty(self.n_dofs, dtype=torch.float64, device=self.device)
         _check(load().ef_load_derivative(self.handle, _dev(nodes, torch.float64, "nodes"), int(n),
                                          _dev(g, torch.float64, "g"), C.c_void_p(b.data_ptr()), _stream_ptr(stream)))
@@ -441,8 +471,11 @@ class Plan:
     def norm_l2(self, nodes, f, n: int, v=None, per_element: bool = False, stream=None):
         """Squared L2 norm of f (values [nq, n_elems, ncomp] at the quadrature points), minus the FE
         function of v if given: (total [1], per-element [n_elems] or None)."""
-        if not f.is_contiguous() or f.dim() != 3:
-            raise TypeError("f must be a contiguous [nq, n_elems, ncomp] tensor")
+        if not isinstance(f, torch.Tensor) or f.dim() != 3:
+            raise ValueError("f must be a [nq, n_elems, ncomp] tensor")
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        self._need_points(f, n, int(f.shape[2]), "f")
+        self._need(v, self.n_dofs, "v")
         total = torch.empty(1, dtype=torch.float64, device=self.device)
         elem = torch.empty(self.n_elems, dtype=torch.float64, device=self.device) if per_element else None
         _check(load().ef_norm_l2(self.handle, _dev(nodes, torch.float64, "nodes"), int(n), int(f.shape[2]),
@@ -453,6 +486,9 @@ class Plan:
 
     def adjoint(self, nodes, coeff, u, v, stream=None):
         """(J, dJ/dnodes, dJ/dcoeff) of J = u^T K u + v^T M v (3D Nedelec)."""
+        self._need_mesh(nodes, coeff)
+        self._need(u, self.n_dofs, "u")
+        self._need(v, self.n_dofs, "v")
         J = torch.empty(1, dtype=torch.float64, device=self.device)
         gx = torch.empty((self.n_nodes, self.dim), dtype=torch.float64, device=self.device)
         gs = torch.empty(self.n_elems, dtype=torch.float64, device=self.device)
@@ -540,6 +576,7 @@ class Batch:
         _check(lib.ef_batch_sizes(self._h, nd, nz))
         self.n_dofs, self.nnz = list(nd), list(nz)
         self.n_elems = [int(e.shape[0]) for e in elems]
+        self.n_nodes = [int(v) for v in n_nodes]
 
     def pattern(self, mesh: int, stream=None):
         rowptr = torch.empty(self.n_dofs[mesh] + 1, dtype=torch.int64, device=self.device)
@@ -549,6 +586,16 @@ class Batch:
         return rowptr, colidx
 
     def bind(self, nodes, coeff, K, M, stream=None):
+        # per-mesh sizes checked here: the C ABI takes plain pointer tables
+        for name, ts, sizes in (("nodes", nodes, [v * self.dim for v in self.n_nodes]),
+                                ("coeff", coeff, self.n_elems), ("K", K, self.nnz), ("M", M, self.nnz)):
+            if ts is None:
+                continue
+            if len(ts) != self.n:
+                raise ValueError(f"{name}: {len(ts)} tensors for {self.n} meshes")
+            for m, (t, z) in enumerate(zip(ts, sizes)):
+                if t is not None and t.numel() != z:
+                    raise ValueError(f"{name}[{m}] has {t.numel()} entries; mesh {m} needs {z}")
         self._bound = (list(nodes), None if coeff is None else list(coeff), list(K), list(M))  # keep alive
         cp = None if coeff is None else _ptr_array(coeff, torch.float64, "coeff", allow_none=True)
         _check(load().ef_batch_bind(self._h, _ptr_array(nodes, torch.float64, "nodes"), cp,

@@ -60,3 +60,31 @@ def test_argument_errors_need_no_gpu():
     assert lib.ef_plan_create(2, 3, 100, 1 << 28, ctypes.c_void_p(16), None, ctypes.byref(h)) == ef.EF_ERR_SIZE
     assert lib.ef_assemble(None, None, None, None, None, None) == ef.EF_ERR_ARG
     assert h.value is None
+
+
+def test_binding_rejects_wrong_sizes_before_the_library():
+    """The C ABI takes plain pointers; the binding checks every tensor against
+    the plan's sizes first (no GPU needed: the checks run before any call)."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    plan = ef.Plan.__new__(ef.Plan)
+    plan.kind, plan.dim, plan.n_nodes, plan.n_elems = ef.EF_NED1, 3, 27, 48
+    plan.n_dofs, plan.nnz, plan.nloc = 98, 1000, 6
+    plan._h = None
+    ok = torch.zeros(27 * 3, dtype=torch.float64)
+    for call in (lambda: plan.assemble(torch.zeros(80, dtype=torch.float64)),
+                 lambda: plan.assemble(ok, torch.zeros(47, dtype=torch.float64)),
+                 lambda: plan.assemble(ok, None, torch.zeros(999, dtype=torch.float64)),
+                 lambda: plan.fe_curl(ok, torch.zeros(97, dtype=torch.float64)),
+                 lambda: plan.load_vector(ok, torch.zeros((8, 48, 2), dtype=torch.float64), 2),
+                 lambda: plan.load_vector(ok, torch.zeros((27, 48, 3), dtype=torch.float64), 2),
+                 lambda: plan.load_derivative(ok, torch.zeros((8, 48, 1), dtype=torch.float64), 2),
+                 lambda: plan.norm_l2(ok, torch.zeros((8, 47, 3), dtype=torch.float64), 2),
+                 lambda: plan.norm_l2_derivative(ok, torch.zeros((8, 48, 3), dtype=torch.float64), 2,
+                                                 torch.zeros(99, dtype=torch.float64)),
+                 lambda: plan.adjoint(ok, None, torch.zeros(98, dtype=torch.float64),
+                                      torch.zeros(97, dtype=torch.float64))):
+        with pytest.raises(ValueError, match="entries|shape"):   # not the closed-handle error
+            call()
