@@ -7,7 +7,8 @@ max(|oracle|, sum |contributions|), through the same ef_assemble launch the
 benchmark times, against the full oracle (about 12 s, 80 s and 50 s on one
 core). The benchmark's batch (256 meshes): sampled meshes against the
 oracle. The benchmark's adjoint (96^3): size-independent identities and
-sampled per-element coefficient gradients against the oracle.
+sampled per-element coefficient gradients and per-node coordinate gradients
+against the oracle.
 """
 import gc
 
@@ -73,7 +74,8 @@ def test_fullsize_adjoint_properties_and_sampled_coefficient_gradient(ora):
     """The benchmark's adjoint workload (96^3, seed 5): identities that hold at
     any size -- sum_e sigma_e dJ/dsigma_e = J, zero net force and torque
     (translation and rotation invariance), sum_i x_i . dJ/dx_i = u^T K u (-1)
-    + v^T M v (K scales like 1/length, M like length) -- and dJ/dsigma_e =
+    + v^T M v (K scales like 1/length, M like length) -- dJ/dx_i against the
+    oracle's adjoint on the star of sampled nodes i, and dJ/dsigma_e =
     u_e^T Khat_e u_e + v_e^T Mhat_e v_e against the oracle's local matrices on
     sampled elements."""
     import torch
@@ -105,6 +107,33 @@ def test_fullsize_adjoint_properties_and_sampled_coefficient_gradient(ora):
     assert np.all(np.abs(torque) <= 1e-10 * (np.abs(nodes).max() * scale.sum()))
     euler = float((nodes * gxn).sum())
     assert abs(euler - (JM - JK)) <= 1e-9 * (abs(JK) + abs(JM))
+    # sampled nodes: dJ/dx_i depends only on the elements around node i, so
+    # the oracle's adjoint on that star (global node ids kept, so the edge
+    # orientations agree; u, v carried over by the edges' node pairs) gives
+    # the full-mesh gradient at node i
+    d2n = plan.topology()[2].cpu().numpy().astype(np.int64)
+    V = nodes.shape[0]
+    full_keys = d2n[:, 0] * V + d2n[:, 1]           # ascending: edges are numbered lexicographically
+    assert np.all(np.diff(full_keys) > 0)
+    rng = np.random.default_rng(5)
+    for i in [0, V // 2, V - 1] + [int(x) for x in rng.integers(0, V, 3)]:
+        star = np.nonzero(np.any(elems == i, axis=1))[0]
+        sub = elems[star]
+        st = ora.topology(NED1, 3, nodes, sub)
+        sk = st["dof2nodes"][:, 0].astype(np.int64) * V + st["dof2nodes"][:, 1]
+        idx = np.searchsorted(full_keys, sk)
+        assert np.array_equal(full_keys[idx], sk)
+        _, gxo, _ = ora.adjoint(NED1, 3, nodes, sub, coeff[star], u[idx], v[idx])
+        # scale: the sum of |each element's contribution| at node i (the net
+        # gradient of an interior node cancels)
+        scale = np.zeros(3)
+        for k in range(len(star)):
+            one = sub[k:k + 1]
+            ot = ora.topology(NED1, 3, nodes, one)
+            ok = np.searchsorted(full_keys, ot["dof2nodes"][:, 0].astype(np.int64) * V + ot["dof2nodes"][:, 1])
+            _, g1, _ = ora.adjoint(NED1, 3, nodes, one, coeff[star[k:k + 1]], u[ok], v[ok])
+            scale += np.abs(g1[i])
+        assert np.all(np.abs(gxn[i] - gxo[i]) <= 1e-12 * scale.max() * len(star)), (i, gxn[i], gxo[i], scale)
     # sampled elements: dJ/dsigma_e from the oracle's local matrices and signs
     topo = ora.topology(NED1, 3, nodes, elems)
     gsn = gs.cpu().numpy()
