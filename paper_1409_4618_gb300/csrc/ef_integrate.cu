@@ -212,16 +212,6 @@ struct FeAffine {
         }
     }
 
-    __device__ __forceinline__ void value(const double* xh, double (&out)[3]) const
-    {
-#pragma unroll
-        for (int r = 0; r < 3; r++) {
-            double x = V0[r];
-#pragma unroll
-            for (int i = 0; i < DIM; i++) x = fma(V[i][r], xh[i], x);
-            out[r] = x;
-        }
-    }
 };
 
 // The rule's points and weights in shared memory, filled by the CTA:
@@ -286,11 +276,22 @@ __global__ void __launch_bounds__(ITPB) k_fe_values(const int32_t* __restrict__ 
     const double det = edge_frame<DIM>(p, B);
     if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
     fe.setup(p, B, det, e2d, __ldg(signbits + e), v, e);
-    for (int q = 0; q < nq; q++) {
-        double val[3];
-        fe.value(table[q], val);
+    // runs of n points along the innermost collapsed coordinate, as in k_norm_l2
+    const int n = r.n;
+    for (int q0 = 0; q0 < nq; q0 += n) {
+        double A[3];
 #pragma unroll
-        for (int c = 0; c < DIM; c++) out[((int64_t)q * T + e) * DIM + c] = val[c];
+        for (int c = 0; c < DIM; c++) {
+            double a = fe.V0[c];
+#pragma unroll
+            for (int i = 0; i < DIM - 1; i++) a = fma(fe.V[i][c], table[q0][i], a);
+            A[c] = a;
+        }
+        for (int q = q0; q < q0 + n; q++) {
+            const double xl = table[q][DIM - 1];
+#pragma unroll
+            for (int c = 0; c < DIM; c++) out[((int64_t)q * T + e) * DIM + c] = fma(fe.V[DIM - 1][c], xl, A[c]);
+        }
     }
 }
 
@@ -320,17 +321,32 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2(const int32_t* __restrict__ el
         if (v) {
             FeAffine<VAR> fe;
             fe.setup(p, B, det, e2d, __ldg(signbits + e), v, e);
-            for (int q = 0; q < nq; q++) {
-                double val[3];
-                fe.value(table[q], val);
-                const double* fq = f + ((int64_t)q * T + e) * DIM;
-                double d2 = 0.0;
+            // The points come in runs of n along the innermost collapsed
+            // coordinate (point q = (i n + j) n + k in 3D, i n + j in 2D):
+            // within a run only xhat_{dim-1} changes, so v_h = A + xhat_{dim-1}
+            // V_{dim-1} with A = V0 + sum_{i < dim-1} xhat_i V_i formed once
+            // per run (DIM FMAs per point instead of DIM^2).
+            const int n = r.n;
+            for (int q0 = 0; q0 < nq; q0 += n) {
+                double A[3];
 #pragma unroll
                 for (int c = 0; c < DIM; c++) {
-                    const double d = __ldg(fq + c) - val[c];
-                    d2 = fma(d, d, d2);
+                    double a = fe.V0[c];
+#pragma unroll
+                    for (int i = 0; i < DIM - 1; i++) a = fma(fe.V[i][c], table[q0][i], a);
+                    A[c] = a;
                 }
-                s = fma(table[q][3], d2, s);
+                for (int q = q0; q < q0 + n; q++) {
+                    const double xl = table[q][DIM - 1];
+                    const double* fq = f + ((int64_t)q * T + e) * DIM;
+                    double d2 = 0.0;
+#pragma unroll
+                    for (int c = 0; c < DIM; c++) {
+                        const double d = __ldg(fq + c) - fma(fe.V[DIM - 1][c], xl, A[c]);
+                        d2 = fma(d, d, d2);
+                    }
+                    s = fma(table[q][3], d2, s);
+                }
             }
         } else {
             for (int q = 0; q < nq; q++) {
