@@ -209,7 +209,9 @@ def run_batched(args, dev, plain_rate):
     """256 independent cubes, n ~ U{8..48} (seed 4, mesh b jittered with seed
     4000 + b), all assembled in one persistent launch or two launches (element
     kernel, sum kernel) over all meshes per step; schedule picked
-    by the library's autotuner. Rate = all elements of the batch per second."""
+    by the library's autotuner. Rate = all elements of the batch per second.
+    Compared with the same meshes as 256 separate ef_assemble calls and with
+    one Kuhn cube of about the batch's element count."""
     import torch
 
     from paper_1409_4618_gb300 import edgefem as ef
@@ -252,6 +254,57 @@ def run_batched(args, dev, plain_rate):
            "plain": "the single-mesh ef_assemble rate of this run", "config": cfg,
            "plan_s": plan_s, "tune_s": tune_s}
     batch.close()
+    del batch
+    torch.cuda.empty_cache()
+    if args.no_batch_baselines:
+        return out
+
+    def timed(fn, steps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    # the same meshes as separate ef_assemble calls, one plan each, into the
+    # same buffers (the default two-pass schedule: 2 launches per mesh)
+    plans = [ef.Plan(2, 3, nd.shape[0], el) for nd, el in zip(nodes, elems)]
+
+    def plain_calls():
+        for pl, nd, c, k, m in zip(plans, nodes, coeff, K, M):
+            ef.ef_assemble(pl.handle, nd, c, k, m, stream)
+
+    ms_p = timed(plain_calls, max(args.batch_steps // 2, 3))
+    for pl in plans:
+        pl.check()
+        pl.close()
+    del plans
+    out["separate_calls"] = {"value": T / (ms_p / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms_p,
+                             "launches_per_step": 2 * len(sizes), "batched_vs": rate / (T / (ms_p / 1e3) / 1e6)}
+    del K, M, nodes, elems, coeff
+    torch.cuda.empty_cache()
+    # one mesh of about the batch's element count (Kuhn cube, 6 n^3 tets)
+    n1 = int(round((T / 6) ** (1.0 / 3.0)))
+    nd1, el1 = mg.kuhn_cube(n1, 0.2, 4)
+    c1 = torch.from_numpy(mg.log_uniform_coeff(4, el1.shape[0])).to(dev)
+    nd1 = torch.from_numpy(nd1).to(dev)
+    pl1 = ef.Plan(2, 3, nd1.shape[0], torch.from_numpy(el1).to(dev))
+    K1 = torch.empty(pl1.nnz, dtype=torch.float64, device=dev)
+    M1 = torch.empty_like(K1)
+    ms_1 = timed(lambda: ef.ef_assemble(pl1.handle, nd1, c1, K1, M1, stream), max(args.batch_steps // 2, 3))
+    pl1.check()
+    T1 = el1.shape[0]
+    out["one_mesh_equal_T"] = {"workload": f"ned3d_kuhn{n1}_jitter0.2", "elements": int(T1),
+                               "value": T1 / (ms_1 / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms_1,
+                               "batched_vs": rate / (T1 / (ms_1 / 1e3) / 1e6)}
+    pl1.close()
+    del K1, M1, pl1, nd1, c1
+    torch.cuda.empty_cache()
     return out
 
 
@@ -764,6 +817,8 @@ def main():
     ap.add_argument("--rt0-steps", type=int, default=20)
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-batch-baselines", action="store_true",
+                    help="skip the batch's comparisons (separate calls, one mesh of equal size)")
     ap.add_argument("--adjoint-steps", type=int, default=50)
     ap.add_argument("--cube", type=int, default=64,
                     help="cubes per axis of the single-mesh workload (smaller values: profiling cases)")
