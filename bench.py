@@ -14,8 +14,9 @@ CUDA events the library records on the launching stream inside the timed
 region), the HBM fraction of the whole step, the clocks seen while timing,
 the CPU oracle timed on this host, and the other workloads: batched (256
 meshes), adjoint (96^3), RT0 (3D 128^3, 2D 32^2) and the vectorised
-integration (L2 error at 27 points per element) and the library share of the
-majorant minimisation (Sec. 4.1) on the 33.5 M-triangle square.
+integration (L2 error at 27 points per element), the library share of the
+majorant minimisation (Sec. 4.1) on the 33.5 M-triangle square, and the 2D
+RT0 and Nedelec assembly on Table 1's L-shaped domain (level 11).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -369,6 +370,65 @@ def run_rt0(args, dev, peaks):
     return out
 
 
+def run_lshape(args, dev, peaks):
+    """The 2D assembly of Table 1: RT0 and Nedelec K and M on the L-shaped
+    domain (0,1)^2 minus (1/2,1)^2 at level L (6 4^L triangles; L = 11:
+    25,165,824 triangles, 37,756,928 edges, the matrix size Table 1 prints),
+    unit coefficient as in the paper, no jitter. Same tuned ef_assemble call
+    and per-kernel CUDA events as the other legs."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.lshape(args.lshape_level)
+    tn = torch.from_numpy(nodes).to(dev)
+    te = torch.from_numpy(elems).to(dev)
+    T, V = elems.shape[0], nodes.shape[0]
+    del elems
+    out = {"workload": f"lshape2d_L{args.lshape_level}", "elements": int(T)}
+    stream = torch.cuda.current_stream()
+    for kind, name in ((1, "rt0"), (2, "nedelec")):
+        plan = ef.Plan(kind, 2, V, te)
+        K = torch.empty(plan.nnz, dtype=torch.float64, device=dev)
+        M = torch.empty_like(K)
+        tuned = plan.tune(tn, None, K, M, reps=3)
+        steps = args.rt0_steps
+        for _ in range(3):
+            ef.ef_assemble(plan.handle, tn, None, K, M, stream)
+        torch.cuda.synchronize()
+        plan.profile(steps)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _nvtx(torch, "timed")
+        a.record(stream)
+        for _ in range(steps):
+            ef.ef_assemble(plan.handle, tn, None, K, M, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        _nvtx(torch, None)
+        ms = a.elapsed_time(b) / steps
+        k1, k2, calls = plan.profile_read()
+        plan.profile(0)
+        plan.check()
+        alg = 12 * T + 16 * V + 16 * plan.nnz
+        gbs = alg / (ms / 1e3) / 1e9
+        leg = {"value": T / (ms / 1e3) / 1e6, "unit": UNIT, "dofs": int(plan.n_dofs), "nnz": int(plan.nnz),
+               "ms_per_step": ms, "tuned_choice": tuned,
+               "kernels_ms": {"first": k1 / max(calls, 1), "second": k2 / max(calls, 1)},
+               "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                       "algorithmic_bytes_per_step": int(alg), "bytes_per_elem": alg / T}}
+        if tuned == 0 and calls:
+            ops = fp64_ops_per_element(kind, 2) * T
+            ach = ops / (k1 / calls / 1e3) / 1e12
+            leg["fp64_element_kernel"] = {"ops_per_elem": fp64_ops_per_element(kind, 2), "achieved": ach,
+                                          "peak": FP64_PEAK_TOPS, "unit": "T fp64-ops/s",
+                                          "frac": ach / FP64_PEAK_TOPS}
+        out[name] = leg
+        plan.close()
+        del K, M
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_integration(args, dev, peaks):
     """Vectorised integration (Sec. 3.1): squared L2 error ||E - v_h||^2 of an
     affine field E against the Nedelec function of a random DOF vector on the
@@ -629,7 +689,7 @@ def run_gpu(args):
         peaks, _ = _peaks()
         legs = {"batched": lambda: run_batched(args, dev, float("nan")), "adjoint": lambda: run_adjoint(args, dev),
                 "rt0": lambda: run_rt0(args, dev, peaks), "integration": lambda: run_integration(args, dev, peaks),
-                "majorant": lambda: run_majorant(args, dev, peaks)}
+                "majorant": lambda: run_majorant(args, dev, peaks), "lshape": lambda: run_lshape(args, dev, peaks)}
         print(json.dumps({"leg": args.only, **legs[args.only]()}), flush=True)
         return 0
     dist = None
@@ -785,6 +845,8 @@ def run_gpu(args):
         line["integration"] = run_integration(args, dev, peaks)
     if not args.no_majorant:
         line["majorant"] = run_majorant(args, dev, peaks)
+    if not args.no_lshape:
+        line["lshape"] = run_lshape(args, dev, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -805,7 +867,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rt0", action="store_true")
-    ap.add_argument("--only", choices=["batched", "adjoint", "rt0", "integration", "majorant"],
+    ap.add_argument("--only", choices=["batched", "adjoint", "rt0", "integration", "majorant", "lshape"],
                     help="run one of the other workloads by itself (profiling)")
     ap.add_argument("--adjoint-cube", type=int, default=96)
     ap.add_argument("--no-integration", action="store_true")
@@ -814,6 +876,9 @@ def main():
     ap.add_argument("--majorant-m", type=int, default=4096,
                     help="squares per axis of the majorant workload (2 m^2 triangles)")
     ap.add_argument("--majorant-steps", type=int, default=5)
+    ap.add_argument("--no-lshape", action="store_true")
+    ap.add_argument("--lshape-level", type=int, default=11,
+                    help="level of the 2D L-shaped workload (6 4^L triangles)")
     ap.add_argument("--rt0-steps", type=int, default=20)
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)

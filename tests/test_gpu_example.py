@@ -35,7 +35,7 @@ def test_documented_example():
     rows = torch.repeat_interleave(torch.arange(plan.n_dofs, device=dev), torch.diff(rowptr))
     uKu = float((u[rows] * K * u[colidx.long()]).sum())
     uMu = float((u[rows] * M * u[colidx.long()]).sum())
-    assert abs(float(J) - (uKu + uMu)) <= 1e-10 * (abs(uKu) + abs(uMu))
+    assert abs(float(J.detach()) - (uKu + uMu)) <= 1e-10 * (abs(uKu) + abs(uMu))
     euler = float((tn.detach() * tn.grad).sum())
     assert abs(euler - (uMu - uKu)) <= 1e-9 * (abs(uKu) + abs(uMu))
     assert x.shape == (27, elems.shape[0], 3) and float(err2[0]) > 0.0
