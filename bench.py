@@ -50,6 +50,9 @@ UNIT = "Melem/s"
 SMS, FP64_PER_CLK_PER_SM, SM_MAX_MHZ = 152, 2, 2070
 FP64_PEAK_TOPS = SMS * FP64_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 L2_BYTES = 129 * 1024 * 1024
+# FP64 peak the legs divide by: the probe's measured DFMA rate once the fp64
+# leg has run (run_gpu runs it first), else the nominal figure above
+FP64_PEAK = {"T_ops_per_s": FP64_PEAK_TOPS, "source": "nominal"}
 # FP64 ops per tetrahedron of the adjoint kernel, counted from the source:
 # B 9, H 18, adj(H) 12, det 9, 1/|det| 8, r^3 2, a 6, a^T H a 9, Whitney
 # coefficients 17, P 30, <P, A> 6, J 6, A P 27, scale factors 14, Gamma 36,
@@ -158,6 +161,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# FP64 instructions per tetrahedron of the Nedelec-3D element kernel as
+# executed (ncu sass counters of one launch on the 48^3 cube, divided by its
+# elements): DADD, DFMA, DMUL.
+ELEMENT_KERNEL_FP64_MIX = {"dadd": 54, "dfma": 46, "dmul": 32}
+FP64_PROBE_ITERS = 100_000
+
+
+def run_fp64_probe(gpu_index: int) -> dict:
+    """This GPU's FP64 pipe throughput, measured by the library's probe kernel
+    (ef_fp64_probe: independent chains of one operation on every SM) for DFMA,
+    DADD and DMUL, three launches each, with the SM clock sampled meanwhile.
+    The DFMA rate is the peak of the element kernels' roofline; the rate for
+    the element kernel's own instruction mix is reported beside it."""
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    rates = {}
+    with ClockSampler(gpu_index) as clk:
+        for name, op in (("dfma", 0), ("dadd", 1), ("dmul", 2)):
+            best = None
+            for _ in range(3):
+                r, ms = ef.ef_fp64_probe(op, FP64_PROBE_ITERS)
+                if best is None or r > best[0]:
+                    best = (r, ms)
+            rates[name] = {"ops_per_s": best[0], "T_ops_per_s": best[0] / 1e12, "ms_per_launch": best[1]}
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz")
+    for v in rates.values():
+        v["ops_per_clk_per_sm"] = v["ops_per_s"] / (SMS * mhz * 1e6) if mhz else None
+    mix = ELEMENT_KERNEL_FP64_MIX
+    t_mix = sum(mix[k] / rates[k]["ops_per_s"] for k in mix)
+    return {"rates": rates, "clocks": clocks, "peak_T_ops_per_s": rates["dfma"]["T_ops_per_s"],
+            "element_mix_T_ops_per_s": sum(mix.values()) / t_mix / 1e12, "element_mix": mix,
+            "how": f"ef_fp64_probe: {SMS} SMs x 4 CTAs x 256 threads x 8 independent chains x "
+                   f"{FP64_PROBE_ITERS} rounds per launch, best of 3, CUDA events on the launching stream"}
+
+
 def fp64_ops_per_element(kind: int, dim: int) -> int:
     """FP64 pipe operations (DADD, DMUL, DFMA each 1) of one element's local
     matrices in the closed forms of csrc/ef_element.cuh, counted from the
@@ -208,11 +247,14 @@ def run_reference(args):
 
 def run_batched(args, dev, plain_rate):
     """256 independent cubes, n ~ U{8..48} (seed 4, mesh b jittered with seed
-    4000 + b), all assembled in one persistent launch or two launches (element
-    kernel, sum kernel) over all meshes per step; schedule picked
-    by the library's autotuner. Rate = all elements of the batch per second.
-    Compared with the same meshes as 256 separate ef_assemble calls and with
-    one Kuhn cube of about the batch's element count."""
+    4000 + b), all assembled per step by one ef_batch_assemble call with the
+    per-mesh buffers passed as pointer tables, captured once in a CUDA graph
+    and timed as graph replays: under the two-launch schedule (element kernel
+    and sum kernel over all meshes) and under the one-launch persistent
+    queue (its best configuration over a small sweep). Rate = all elements of
+    the batch per second, of the faster schedule. Compared with the same
+    meshes as 256 separate ef_assemble calls and with one Kuhn cube of about
+    the batch's element count."""
     import torch
 
     from paper_1409_4618_gb300 import edgefem as ef
@@ -231,29 +273,90 @@ def run_batched(args, dev, plain_rate):
     M = [torch.empty(z, dtype=torch.float64, device=dev) for z in batch.nnz]
     batch.bind(nodes, coeff, K, M)
     t0 = time.perf_counter()
-    cfg = batch.tune(reps=2)
+    tuned = batch.tune(reps=2)
     tune_s = time.perf_counter() - t0
+    tabs = batch.tables(nodes, coeff, K, M)
     stream = torch.cuda.current_stream()
+    T = int(sum(batch.n_elems))
+
+    def graph_ms(steps):
+        """ms per replay of a CUDA graph holding one ef_batch_assemble call."""
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            batch.assemble_tables(tabs, stream=side)
+            side.synchronize()
+            with torch.cuda.graph(g, stream=side):
+                batch.assemble_tables(tabs, stream=side)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        batch.check()
+        del g
+        return a.elapsed_time(b) / steps
+
+    schedules = {}
+    batch.set_config(two_launch=1)
+    schedules["two_launch"] = {"ms_per_step": graph_ms(max(args.batch_steps // 2, 3)), "launches_per_step": 2 + (
+        len(sizes) + 63) // 64, "config": batch.config()}
+    best = None
+    for tile in (128, 256):
+        for su in (512, 2048):
+            for ec in (0, 1):
+                for lf in (0, 1):
+                    batch.set_config(elems_per_tile=tile, sum_tile=max(su, tile), elem_ctas=ec, dynamic=1,
+                                     largest_first=lf, two_launch=0, ctas_per_sm=0)
+                    ms = graph_ms(3)
+                    if best is None or ms < best[0]:
+                        best = (ms, batch.config())
+    batch.set_config(**best[1])
+    schedules["persistent"] = {"ms_per_step": graph_ms(max(args.batch_steps // 2, 3)),
+                               "launches_per_step": 1 + (len(sizes) + 63) // 64, "config": best[1]}
+    for v in schedules.values():
+        v["value"] = T / (v["ms_per_step"] / 1e3) / 1e6
+        v["unit"] = UNIT
+    fast = min(schedules, key=lambda k: schedules[k]["ms_per_step"])
+    # the timed steps: the faster schedule, graph replays inside the NVTX range
+    batch.set_config(**schedules[fast]["config"])
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        batch.assemble_tables(tabs, stream=side)
+        side.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            batch.assemble_tables(tabs, stream=side)
+    torch.cuda.synchronize()
     for _ in range(3):
-        batch.assemble(stream)
-    batch.check()
+        g.replay()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     _nvtx(torch, "timed")
     e0.record(stream)
     for _ in range(args.batch_steps):
-        batch.assemble(stream)
+        g.replay()
     e1.record(stream)
     torch.cuda.synchronize()
     _nvtx(torch, None)
     batch.check()
+    del g
     ms = e0.elapsed_time(e1) / args.batch_steps
-    T = int(sum(batch.n_elems))
     rate = T / (ms / 1e3) / 1e6
     out = {"value": rate, "unit": UNIT, "meshes": len(sizes), "elements": T, "nnz": int(sum(batch.nnz)),
-           "ms_per_step": ms, "launches_per_step": 2 if cfg.get("two_launch") else 1, "vs_plain": rate / plain_rate,
-           "plain": "the single-mesh ef_assemble rate of this run", "config": cfg,
-           "plan_s": plan_s, "tune_s": tune_s}
+           "ms_per_step": ms, "graph": True, "call": "ef_batch_assemble (per-call pointer tables)",
+           "schedule": fast, "launches_per_step": schedules[fast]["launches_per_step"],
+           "schedules": schedules, "persistent_vs_two_launch":
+               schedules["two_launch"]["ms_per_step"] / schedules["persistent"]["ms_per_step"],
+           "vs_plain": rate / plain_rate, "plain": "the single-mesh ef_assemble rate of this run",
+           "tuned_config": tuned, "plan_s": plan_s, "tune_s": tune_s}
     batch.close()
     del batch
     torch.cuda.empty_cache()
@@ -362,8 +465,9 @@ def run_rt0(args, dev, peaks):
             ops = fp64_ops_per_element(1, dim) * T
             ach = ops / (k1 / calls / 1e3) / 1e12
             out[name]["fp64_element_kernel"] = {"ops_per_elem": fp64_ops_per_element(1, dim), "achieved": ach,
-                                                "peak": FP64_PEAK_TOPS, "unit": "T fp64-ops/s",
-                                                "frac": ach / FP64_PEAK_TOPS}
+                                                "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-ops/s",
+                                                "frac": ach / FP64_PEAK["T_ops_per_s"],
+                                                "peak_source": FP64_PEAK["source"]}
         plan.close()
         del K, M
         torch.cuda.empty_cache()
@@ -420,8 +524,9 @@ def run_lshape(args, dev, peaks):
             ops = fp64_ops_per_element(kind, 2) * T
             ach = ops / (k1 / calls / 1e3) / 1e12
             leg["fp64_element_kernel"] = {"ops_per_elem": fp64_ops_per_element(kind, 2), "achieved": ach,
-                                          "peak": FP64_PEAK_TOPS, "unit": "T fp64-ops/s",
-                                          "frac": ach / FP64_PEAK_TOPS}
+                                          "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-ops/s",
+                                          "frac": ach / FP64_PEAK["T_ops_per_s"],
+                                          "peak_source": FP64_PEAK["source"]}
         out[name] = leg
         plan.close()
         del K, M
@@ -609,8 +714,9 @@ def run_adjoint(args, dev):
            "plain_same_mesh": {"value": T / (ms_asm / 1e3) / 1e6, "ms_per_step": ms_asm},
            "vs_plain": ms_asm / ms_adj,
            "fp64": {"ops_per_elem": ADJOINT_FP64_OPS_PER_TET, "achieved": ops / (ms_adj / 1e3) / 1e12,
-                    "peak": FP64_PEAK_TOPS, "unit": "T fp64-ops/s",
-                    "frac": ops / (ms_adj / 1e3) / 1e12 / FP64_PEAK_TOPS,
+                    "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-ops/s",
+                    "frac": ops / (ms_adj / 1e3) / 1e12 / FP64_PEAK["T_ops_per_s"],
+                    "peak_source": FP64_PEAK["source"],
                     "note": "whole ef_adjoint call (element kernel ~92 % of it)"}}
     plan.close()
     return out
@@ -698,6 +804,8 @@ def run_gpu(args):
 
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    probe = run_fp64_probe(local)
+    FP64_PEAK.update(T_ops_per_s=probe["peak_T_ops_per_s"], source="measured (bench fp64 leg: ef_fp64_probe DFMA)")
     nodes, elems, coeff = _workload()
     w = WORKLOAD
     tn = torch.from_numpy(nodes).to(dev)
@@ -809,13 +917,24 @@ def run_gpu(args):
         dom_name, dom_ms, dom_ops, traffic = "ef_assemble (" + path + ")", one if k_calls else ms_step, \
             elem_ops + sum_ops, None
     achieved_ops = dom_ops / (dom_ms / 1e3) / 1e12
+    peak = probe["peak_T_ops_per_s"]
+    exec_ops = sum(ELEMENT_KERNEL_FP64_MIX.values()) * T if dom_ops == elem_ops else None
     roofline = {
-        "bound": "alu", "unit": "T fp64-ops/s", "achieved": achieved_ops, "peak": FP64_PEAK_TOPS,
-        "frac": achieved_ops / FP64_PEAK_TOPS, "traffic": traffic,
-        "peak_source": f"{SMS} SMs x {FP64_PER_CLK_PER_SM} FP64 ops/clk/SM x {SM_MAX_MHZ} MHz "
-                       "(DADD, DMUL, DFMA = 1 op each)",
+        "bound": "alu", "unit": "T fp64-ops/s", "achieved": achieved_ops, "peak": peak,
+        "frac": achieved_ops / peak, "traffic": traffic,
+        "peak_source": "measured (bench fp64 leg: ef_fp64_probe DFMA lane-ops/s on this GPU, "
+                       f"median SM clock {probe['clocks'].get('sm_mhz')} MHz during the probe)",
+        "peak_nominal": FP64_PEAK_TOPS,
+        "peak_nominal_source": f"{SMS} SMs x {FP64_PER_CLK_PER_SM} FP64 ops/clk/SM x {SM_MAX_MHZ} MHz",
         "kernel": dom_name, "ms_per_launch": dom_ms,
         "fp64_ops_per_launch": int(dom_ops), "fp64_ops_per_elem": dom_ops / T,
+        "fp64_ops_source": "counted from the source (csrc/ef_element.cuh)",
+        "executed": (None if exec_ops is None else
+                     {"fp64_ops_per_elem": exec_ops / T, "source": "ncu sass FP64 instruction counters, 48^3",
+                      "achieved": exec_ops / (dom_ms / 1e3) / 1e12,
+                      "frac": exec_ops / (dom_ms / 1e3) / 1e12 / peak,
+                      "frac_of_mix_peak": exec_ops / (dom_ms / 1e3) / 1e12 / probe["element_mix_T_ops_per_s"]}),
+        "fp64_probe": probe,
         "kernels": kernels,
         "hbm_step": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved_gbs / peaks["hbm_gbs"],

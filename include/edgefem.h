@@ -63,7 +63,7 @@ extern "C" {
 #define EF_ERR_OOM (-5)          /* device allocation failed */
 #define EF_ERR_CUDA (-6)         /* a CUDA runtime call failed (see ef_last_error) */
 #define EF_ERR_TIMEOUT (-7)      /* a bounded device-side wait gave up */
-#define EF_ERR_SIZE (-8)         /* mesh beyond the 32-bit index limits stated per call */
+#define EF_ERR_SIZE (-8)         /* size beyond a limit stated per call (32-bit indices, fixed scratch) */
 
 typedef enum { EF_RT0 = 1, EF_NED1 = 2 } ef_kind;
 
@@ -223,18 +223,22 @@ int ef_assemble_host(ef_plan* plan, const double* h_nodes, const double* h_coeff
  * cudaFree may cause, and applications whose device memory belongs to
  * another allocator with a fixed budget.
  *
- * Same result as ef_assemble (the same sums in the same order, so the same
- * bits), computed by the two-pass kernels with the element matrices kept in
+ * Same result as ef_assemble_two_pass (the same sums in the same order, so
+ * the same bits), computed by two kernels with the element matrices kept in
  * one library-wide static device array of EF_NOALLOC_SCRATCH_BYTES instead
  * of the plan's own scratch. No cudaMalloc, cudaFree or other allocating
  * routine is called. The array exists on every GPU that loads the library
  * and stays there until the process exits.
  *   Limit: n_elems * nloc (nloc+1)/2 * 16 bytes must fit in the array
  *   (3D Nedelec: 199,728 elements; 3D RT0: 419,430; 2D: 699,050); larger
- *   plans get EF_ERR_SIZE and nothing is launched.
+ *   plans get EF_ERR_SIZE (ef_last_error names the bytes needed) and nothing
+ *   is launched.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *   life of the process; make that first call before any stream capture.
+ *   The kept address belongs to the device's primary context: after
+ *   cudaDeviceReset (or any other teardown of that context) this entry point
+ *   must not be called again in the process.
  *   Every call uses the same array and leaves its contents there; nothing in
  *   it has to start at zero, because each call overwrites every entry it
  *   reads. Calls whose work overlaps on the GPU (on different streams, or on
@@ -343,7 +347,8 @@ int ef_load_derivative(ef_plan* plan, const double* d_nodes, int n, const double
 
 /*
  * A batch holds independent meshes of one kind and dimension, each with its
- * own plan and its own CSR. ef_batch_assemble assembles all of them either in
+ * own plan and its own CSR. ef_batch_assemble (buffers passed per call) and
+ * ef_batch_assemble_bound (buffers bound once) assemble all of them either in
  * ONE persistent kernel launch over (mesh, element tile) and (mesh, sum tile)
  * work, where a sum tile starts once the element tiles it depends on are done
  * (a bounded wait; EF_ERR_TIMEOUT from ef_batch_check if a wait gave up), or
@@ -357,7 +362,8 @@ typedef struct ef_batch ef_batch;
 typedef struct {
     int32_t elems_per_tile;  /* elements per element tile = threads per CTA: 128 or 256 */
     int32_t sum_tile;        /* upper nonzeros per sum tile */
-    int32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x number of SMs */
+    int32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x number of SMs (0 in ef_batch_set_config:
+                                as many as fit) */
     int32_t dynamic;         /* 1: tiles by an integer ticket; 0: static stride blockIdx + k gridDim */
     int32_t largest_first;   /* 1: meshes in order of decreasing size; 0: as given */
     int32_t elem_ctas;       /* 0: every CTA takes tiles of both kinds from one interleaved queue;
@@ -376,7 +382,8 @@ int ef_batch_create(int kind, int dim, int n_meshes, const int64_t* n_nodes, con
 int ef_batch_sizes(const ef_batch* batch, int64_t* n_dofs, int64_t* nnz);
 /* CSR pattern of one mesh (as ef_plan_pattern). */
 int ef_batch_pattern(const ef_batch* batch, int mesh, int64_t* d_rowptr, int32_t* d_colidx, void* stream);
-/* Bind the per-mesh device buffers used by ef_batch_assemble: host arrays
+/* Bind the per-mesh device buffers used by ef_batch_assemble_bound and the
+ * tuner: host arrays
  * [n_meshes] of device pointers to nodes (n_nodes x dim), coefficients
  * (n_elems, or a NULL array / NULL entries for 1) and K, M values (nnz).
  * Copies the pointer tables to the device and synchronises `stream`. */
@@ -386,7 +393,7 @@ int ef_batch_bind(ef_batch* batch, const double* const* d_nodes, const double* c
  * launches with two_launch set. Asynchronous, no allocation, no host
  * synchronisation; capturable in a CUDA graph. Calls that overlap on the GPU
  * race. EF_ERR_ARG if nothing is bound. */
-int ef_batch_assemble(const ef_batch* batch, void* stream);
+int ef_batch_assemble_bound(const ef_batch* batch, void* stream);
 /* Autotuner: times each candidate schedule `reps` times on the bound buffers
  * (the two-launch form; the persistent launch with 128/256 elements per tile,
  * 512/2048 nonzeros per sum tile, 0-2 element-only CTAs per four, dynamic or
@@ -398,6 +405,32 @@ int ef_batch_set_config(ef_batch* batch, const ef_batch_config_t* cfg, void* str
 /* Synchronise `stream`; EF_ERR_DEGENERATE / EF_ERR_TIMEOUT if met since the last check. */
 int ef_batch_check(ef_batch* batch, void* stream);
 void ef_batch_destroy(ef_batch* batch);
+
+/*
+ * The batched calls with the buffers passed per call (the batch plan is the
+ * same object as ef_batch; every ef_batch_* call above accepts it):
+ *   ef_batch_plan_create: as ef_batch_create (per-mesh plans: the topology
+ *     and CSR pattern of Sec. 3 for each mesh). Synchronises `stream`.
+ *   ef_batch_assemble: assembles every mesh m into d_Kval[m], d_Mval[m]
+ *     (nnz_m doubles each) from d_nodes[m] (n_nodes_m x dim) and d_coeff[m]
+ *     (n_elems_m, or NULL; d_coeff itself may be NULL for all ones). The four
+ *     arguments are HOST arrays [n_meshes] of device pointers; they are read
+ *     during the call and need not outlive it. The call writes them into the
+ *     plan's device descriptors by kernels on `stream` (one per 64 meshes),
+ *     then runs the schedule the plan has selected (ef_batch_set_config /
+ *     ef_batch_tune): same values as ef_plan-wise ef_assemble, bit for bit.
+ *     Asynchronous; no allocation, no host synchronisation, no host-to-device
+ *     copy: capturable in a CUDA graph, a replay reusing the pointers given
+ *     at capture. Calls that overlap on the GPU race on the descriptors.
+ *     Errors: EF_ERR_ARG (NULL table, or NULL entry for a non-empty mesh).
+ *   ef_batch_plan_destroy: as ef_batch_destroy.
+ */
+typedef struct ef_batch ef_batch_plan;
+int ef_batch_plan_create(int kind, int dim, int n_meshes, const int64_t* n_nodes, const int64_t* n_elems,
+                         const int32_t* const* d_elems, void* stream, ef_batch_plan** out);
+int ef_batch_assemble(const ef_batch_plan* batch, const double* const* d_nodes, const double* const* d_coeff,
+                      double* const* d_Kval, double* const* d_Mval, void* stream);
+void ef_batch_plan_destroy(ef_batch_plan* batch);
 
 /* ---- one-shot convenience calls ------------------------------------------ */
 
@@ -419,6 +452,22 @@ int rt0_assemble(int dim, const double* d_nodes, int64_t n_nodes, const int32_t*
 int ned_assemble(int dim, const double* d_nodes, int64_t n_nodes, const int32_t* d_elems, int64_t n_elems,
                  const double* d_coeff, ef_csr* out, void* stream);
 void ef_csr_free(ef_csr* csr);
+
+/* ---- measurement -------------------------------------------------------------- */
+
+/*
+ * ef_fp64_probe -- not part of the paper's method: measures the throughput of
+ * this GPU's FP64 pipe, the bound of the element kernels (their work is a
+ * stream of FP64 additions, multiplications and fused multiply-adds, see
+ * Sec. 2.4's local matrices). op = 0: DFMA, 1: DADD, 2: DMUL. Every thread
+ * of a grid of 4 CTAs of 256 threads per SM runs 8 independent chains of
+ * `iters` operations; *ops_per_s receives the lane operations per second
+ * (one per DFMA), *ms (may be NULL) the timed launch's duration. d_sink: one
+ * device double the kernel may write (it never does for these inputs).
+ * Launches a short warm-up and the timed kernel on `stream`, synchronises it.
+ * Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ */
+int ef_fp64_probe(int op, int64_t iters, double* d_sink, double* ops_per_s, double* ms, void* stream);
 
 /* ---- diagnostics ------------------------------------------------------------ */
 

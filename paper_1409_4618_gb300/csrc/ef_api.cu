@@ -602,7 +602,7 @@ const char* ef_status_string(int status)
         case EF_ERR_OOM: return "device out of memory";
         case EF_ERR_CUDA: return "CUDA error";
         case EF_ERR_TIMEOUT: return "bounded device wait timed out";
-        case EF_ERR_SIZE: return "mesh exceeds the 32-bit index limits";
+        case EF_ERR_SIZE: return "size beyond a limit of the call (32-bit indices or a fixed scratch array)";
         default: return "unknown status";
     }
 }

@@ -35,6 +35,32 @@ void destroy(ef_batch* b)
     delete b;
 }
 
+// Per-call buffers of ef_batch_assemble: the four pointer tables of up to
+// BIND_CHUNK meshes travel as one kernel's parameters (2 KiB, inside the
+// classic 4 KiB limit) and are written into the device descriptors on the
+// call's stream, so the call needs no host synchronisation, no allocation
+// and no copy from host memory, and a captured call keeps the tables it was
+// captured with.
+constexpr int BIND_CHUNK = 64;
+struct BindChunk {
+    int first, count;
+    const double* nodes[BIND_CHUNK];
+    const double* coeff[BIND_CHUNK];
+    double* K[BIND_CHUNK];
+    double* M[BIND_CHUNK];
+};
+
+__global__ void k_bind_tables(QueueMesh* __restrict__ md, const BindChunk c)
+{
+    const int i = threadIdx.x;
+    if (i >= c.count) return;
+    QueueMesh& d = md[c.first + i];
+    d.nodes = c.nodes[i];
+    d.coeff = c.coeff[i];
+    d.K = c.K[i];
+    d.M = c.M[i];
+}
+
 }  // namespace
 }  // namespace ef
 
@@ -114,11 +140,43 @@ int ef_batch_bind(ef_batch* b, const double* const* d_nodes, const double* const
     return EF_OK;
 }
 
-int ef_batch_assemble(const ef_batch* b, void* stream)
+int ef_batch_assemble_bound(const ef_batch* b, void* stream)
 {
     if (!b || !b->bound) return EF_ERR_ARG;
     return queue_launch(&b->queue, QueueArgs(), (cudaStream_t)stream);
 }
+
+int ef_batch_plan_create(int kind, int dim, int n_meshes, const int64_t* n_nodes, const int64_t* n_elems,
+                         const int32_t* const* d_elems, void* stream, ef_batch_plan** out)
+{
+    return ef_batch_create(kind, dim, n_meshes, n_nodes, n_elems, d_elems, stream, out);
+}
+
+int ef_batch_assemble(const ef_batch_plan* b, const double* const* d_nodes, const double* const* d_coeff,
+                      double* const* d_Kval, double* const* d_Mval, void* stream)
+{
+    if (!b || !d_nodes || !d_Kval || !d_Mval) return EF_ERR_ARG;
+    for (int m = 0; m < b->n; m++)
+        if (b->plans[m]->T > 0 && (!d_nodes[m] || !d_Kval[m] || !d_Mval[m])) return EF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int m0 = 0; m0 < b->n; m0 += BIND_CHUNK) {
+        BindChunk c;
+        memset(&c, 0, sizeof(c));
+        c.first = m0;
+        c.count = b->n - m0 < BIND_CHUNK ? b->n - m0 : BIND_CHUNK;
+        for (int i = 0; i < c.count; i++) {
+            c.nodes[i] = d_nodes[m0 + i];
+            c.coeff[i] = d_coeff ? d_coeff[m0 + i] : nullptr;
+            c.K[i] = d_Kval[m0 + i];
+            c.M[i] = d_Mval[m0 + i];
+        }
+        k_bind_tables<<<1, BIND_CHUNK, 0, s>>>(b->queue.d_mesh, c);
+    }
+    EF_CUDA(cudaGetLastError());
+    return queue_launch(&b->queue, QueueArgs(), s);
+}
+
+void ef_batch_plan_destroy(ef_batch_plan* b) { destroy(b); }
 
 int ef_batch_get_config(const ef_batch* b, ef_batch_config_t* cfg)
 {
@@ -135,8 +193,9 @@ int ef_batch_set_config(ef_batch* b, const ef_batch_config_t* cfg, void* stream)
     if (cfg->two_launch != 0 && cfg->two_launch != 1) return EF_ERR_ARG;
     if (cfg->sum_tile < cfg->elems_per_tile || cfg->sum_tile > (1 << 20)) return EF_ERR_ARG;
     const int maxc = queue_max_ctas_per_sm(b->variant, cfg->elems_per_tile);
-    if (cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > maxc) return EF_ERR_ARG;
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > maxc) return EF_ERR_ARG;
     b->queue.cfg = *cfg;
+    if (cfg->ctas_per_sm == 0) b->queue.cfg.ctas_per_sm = maxc;   // 0: as many as fit
     return queue_build(&b->queue, b->plans, (cudaStream_t)stream);
 }
 

@@ -32,6 +32,8 @@ enum : int { ST_DEGENERATE = 1, ST_RANGE = 2, ST_REPEAT = 4, ST_TIMEOUT = 8 };
 
 // Error helpers ------------------------------------------------------------
 void set_last_error(const char* where, cudaError_t err);
+// printf-style text for ef_last_error (argument and size refusals)
+void set_last_message(const char* fmt, ...);
 #define EF_CUDA(call)                                    \
     do {                                                 \
         cudaError_t e_ = (call);                         \

@@ -108,7 +108,12 @@ extern "C" int ef_assemble_noalloc(const ef_plan* plan, const double* d_nodes, c
     if (!plan) return EF_ERR_ARG;
     if (plan->T > 0 && (!d_nodes || !d_Kval || !d_Mval)) return EF_ERR_ARG;
     const size_t need = (size_t)plan->T * plan->np * 2 * sizeof(double);
-    if (need > kScratchBytes) return EF_ERR_SIZE;
+    if (need > kScratchBytes) {
+        set_last_message("ef_assemble_noalloc: this plan needs %zu bytes of scratch, more than the "
+                         "EF_NOALLOC_SCRATCH_BYTES = %zu of the static array",
+                         need, kScratchBytes);
+        return EF_ERR_SIZE;
+    }
     if (plan->T == 0) return EF_OK;
     double* local = nullptr;
     EF_TRY(scratch_address(&local));

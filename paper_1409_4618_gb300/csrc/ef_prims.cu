@@ -4,6 +4,7 @@
 // Both are reduce-then-scan designs with no inter-CTA waiting: each pass is
 // a sequence of ordinary launches on one stream, so no launch can wait on
 // another CTA.
+#include <stdarg.h>
 #include <stdio.h>
 
 #include "ef_internal.cuh"
@@ -15,6 +16,14 @@ static thread_local char g_last_error[256] = "";
 void set_last_error(const char* where, cudaError_t err)
 {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(err));
+}
+
+void set_last_message(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
 }
 
 const char* last_error_text() { return g_last_error; }

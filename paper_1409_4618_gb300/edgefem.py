@@ -111,7 +111,10 @@ def load():
             "ef_batch_sizes": ([P, P, P], I),
             "ef_batch_pattern": ([P, I, P, P, P], I),
             "ef_batch_bind": ([P, P, P, P, P, P], I),
-            "ef_batch_assemble": ([P, P], I),
+            "ef_batch_assemble_bound": ([P, P], I),
+            "ef_batch_plan_create": ([I, I, I, P, P, P, P, C.POINTER(P)], I),
+            "ef_batch_assemble": ([P, P, P, P, P, P], I),
+            "ef_batch_plan_destroy": ([P], None),
             "ef_batch_tune": ([P, I, C.POINTER(BatchConfig), P], I),
             "ef_batch_get_config": ([P, C.POINTER(BatchConfig)], I),
             "ef_batch_set_config": ([P, C.POINTER(BatchConfig), P], I),
@@ -125,6 +128,7 @@ def load():
             "ef_norm_l2_derivative": ([P, P, I, P, P, P, P, P], I),
             "ef_load_vector": ([P, P, I, P, P, P], I),
             "ef_load_derivative": ([P, P, I, P, P, P], I),
+            "ef_fp64_probe": ([I, I64, P, C.POINTER(C.c_double), C.POINTER(C.c_double), P], I),
             "ef_status_string": ([I], C.c_char_p),
             "ef_last_error": ([], C.c_char_p),
         }
@@ -239,6 +243,15 @@ def ef_adjoint(plan, nodes, coeff, u, v, J=None, grad_nodes=None, grad_coeff=Non
                              _dev(u, torch.float64, "u"), _dev(v, torch.float64, "v"), _dev(J, torch.float64, "J"),
                              _dev(grad_nodes, torch.float64, "grad_nodes"), _dev(grad_coeff, torch.float64, "grad_coeff"),
                              _stream_ptr(stream)))
+
+
+def ef_fp64_probe(op: int, iters: int, stream=None) -> tuple[float, float]:
+    """(lane operations per second, ms) of the FP64 pipe for op 0 = DFMA, 1 = DADD, 2 = DMUL."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rate, ms = C.c_double(), C.c_double()
+    _check(load().ef_fp64_probe(int(op), int(iters), C.c_void_p(sink.data_ptr()), C.byref(rate), C.byref(ms),
+                                _stream_ptr(stream)))
+    return rate.value, ms.value
 
 
 def ef_plan_check(plan, stream=None):
@@ -386,6 +399,13 @@ class Plan:
         self._need_mesh(nodes, coeff, K, M)
         K, M = self._vals(K, M)
         ef_assemble_two_pass(self.handle, nodes, coeff, K, M, stream)
+        return K, M
+
+    def assemble_noalloc(self, nodes, coeff=None, K=None, M=None, stream=None):
+        """ef_assemble_noalloc: the library allocates nothing (pass K and M to allocate nothing here either)."""
+        self._need_mesh(nodes, coeff, K, M)
+        K, M = self._vals(K, M)
+        ef_assemble_noalloc(self.handle, nodes, coeff, K, M, stream)
         return K, M
 
     def assemble2(self, nodes, coeff_K=None, coeff_M=None, K=None, M=None, stream=None):
@@ -560,7 +580,9 @@ def energy(plan: "Plan", nodes: torch.Tensor, coeff, u: torch.Tensor, v: torch.T
 
 
 class Batch:
-    """Many independent meshes assembled by one persistent launch (ef_batch_*)."""
+    """Many independent meshes, each to its own CSR (ef_batch_plan_create / ef_batch_assemble and the other
+    ef_batch_* calls): buffers either passed per call (tables + assemble_tables) or bound once (bind +
+    assemble)."""
 
     def __init__(self, kind: int, dim: int, n_nodes, elems, stream=None):
         lib = load()
@@ -570,7 +592,7 @@ class Batch:
         ne = (C.c_int64 * self.n)(*[int(e.shape[0]) for e in elems])
         ep = _ptr_array(elems, torch.int32, "elems")
         self._h = C.c_void_p()
-        _check(lib.ef_batch_create(kind, dim, self.n, nn, ne, ep, _stream_ptr(stream), C.byref(self._h)))
+        _check(lib.ef_batch_plan_create(kind, dim, self.n, nn, ne, ep, _stream_ptr(stream), C.byref(self._h)))
         nd = (C.c_int64 * self.n)()
         nz = (C.c_int64 * self.n)()
         _check(lib.ef_batch_sizes(self._h, nd, nz))
@@ -585,7 +607,7 @@ class Batch:
                                        _dev(colidx, torch.int32, "colidx"), _stream_ptr(stream)))
         return rowptr, colidx
 
-    def bind(self, nodes, coeff, K, M, stream=None):
+    def _check_sizes(self, nodes, coeff, K, M):
         # per-mesh sizes checked here: the C ABI takes plain pointer tables
         for name, ts, sizes in (("nodes", nodes, [v * self.dim for v in self.n_nodes]),
                                 ("coeff", coeff, self.n_elems), ("K", K, self.nnz), ("M", M, self.nnz)):
@@ -596,6 +618,9 @@ class Batch:
             for m, (t, z) in enumerate(zip(ts, sizes)):
                 if t is not None and t.numel() != z:
                     raise ValueError(f"{name}[{m}] has {t.numel()} entries; mesh {m} needs {z}")
+
+    def bind(self, nodes, coeff, K, M, stream=None):
+        self._check_sizes(nodes, coeff, K, M)
         self._bound = (list(nodes), None if coeff is None else list(coeff), list(K), list(M))  # keep alive
         cp = None if coeff is None else _ptr_array(coeff, torch.float64, "coeff", allow_none=True)
         _check(load().ef_batch_bind(self._h, _ptr_array(nodes, torch.float64, "nodes"), cp,
@@ -603,7 +628,19 @@ class Batch:
                                     _stream_ptr(stream)))
 
     def assemble(self, stream=None):
-        _check(load().ef_batch_assemble(self._h, _stream_ptr(stream)))
+        """ef_batch_assemble_bound: every mesh into the buffers given to bind()."""
+        _check(load().ef_batch_assemble_bound(self._h, _stream_ptr(stream)))
+
+    def tables(self, nodes, coeff, K, M):
+        """Per-mesh pointer tables for assemble_tables (sizes checked here); holds the tensors alive."""
+        self._check_sizes(nodes, coeff, K, M)
+        cp = None if coeff is None else _ptr_array(coeff, torch.float64, "coeff", allow_none=True)
+        return (_ptr_array(nodes, torch.float64, "nodes"), cp, _ptr_array(K, torch.float64, "K"),
+                _ptr_array(M, torch.float64, "M"), (list(nodes), coeff, list(K), list(M)))
+
+    def assemble_tables(self, tables, stream=None):
+        """ef_batch_assemble: every mesh into the buffers of `tables` (from tables()), passed with the call."""
+        _check(load().ef_batch_assemble(self._h, tables[0], tables[1], tables[2], tables[3], _stream_ptr(stream)))
 
     def tune(self, reps: int = 3, stream=None) -> dict:
         cfg = BatchConfig()
@@ -624,7 +661,7 @@ class Batch:
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value is not None:
-            load().ef_batch_destroy(self._h)
+            load().ef_batch_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):

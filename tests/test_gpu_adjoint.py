@@ -1,6 +1,7 @@
 """GPU adjoint of J = u^T K u + v^T M v (3D Nedelec), through the C ABI.
 
-Checked against the oracle's forward-mode (dual number) adjoint, against
+Checked against the oracle's forward-mode (dual number) adjoint (every node
+gradient within 1e-11 of the sum of its elements' absolute gradients), against
 central finite differences of J computed from the GPU's own assembled
 matrices on the 4^3 sub-mesh (seed 55), and for bitwise run-to-run
 reproducibility.
@@ -9,6 +10,7 @@ import numpy as np
 import pytest
 
 from paper_1409_4618_gb300 import meshgen as mg
+from tests._scales import adjoint_node_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -57,8 +59,10 @@ def test_adjoint_vs_oracle(ora, n, seed, shuffle):
     Jo, gxo, gso = ora.adjoint(NED1, 3, nodes, elems, coeff, u, v)
     Jg, gxg, gsg = _gpu_adjoint(nodes, elems, coeff, u, v)
     assert abs(Jg - Jo) <= 1e-12 * abs(Jo) * 10
-    scale_x = np.abs(gxo).max()
-    np.testing.assert_allclose(gxg, gxo, rtol=0, atol=1e-11 * scale_x)
+    # per node and coordinate: within 1e-11 of sum_K |dJ_K/dx| (the element
+    # gradients summed into it; their cancellation is what makes an entry small)
+    scale_x = adjoint_node_scale(ora, NED1, 3, nodes, elems, coeff, u, v)
+    assert np.all(np.abs(gxg - gxo) <= 1e-11 * scale_x), float((np.abs(gxg - gxo) / scale_x).max())
     np.testing.assert_allclose(gsg, gso, rtol=1e-11, atol=1e-13 * np.abs(gso).max())
 
 

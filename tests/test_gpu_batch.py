@@ -128,3 +128,59 @@ def test_batch_in_cuda_graph():
     batch.check()
     _same_bits(K, M, ref)
     batch.close()
+
+
+@pytest.mark.parametrize("two_launch", [1, 0])
+def test_batch_plan_per_call_buffers_and_graph(two_launch):
+    """ef_batch_plan_create / ef_batch_assemble with the per-mesh buffers passed
+    as pointer tables on each call: two calls into two different sets of
+    buffers, then a CUDA graph of the call replayed twice with new
+    coefficients written into the captured buffers, each equal bit for bit to
+    per-mesh ef_assemble; under the two-launch and the persistent schedule."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    meshes = _meshes(NED1, 70, 1, 7, 11)           # more than the 64 meshes of one descriptor kernel
+    batch, nodes, elems, coeff, K, M, ref = _setup(NED1, meshes)
+    batch.set_config(two_launch=two_launch)
+    K2 = [torch.full_like(k, float("nan")) for k in K]
+    M2 = [torch.full_like(m, float("nan")) for m in M]
+    for k in K + M:
+        k.fill_(float("nan"))
+    batch.assemble_tables(batch.tables(nodes, coeff, K2, M2))
+    batch.assemble_tables(batch.tables(nodes, coeff, K, M))
+    batch.check()
+    _same_bits(K, M, ref)
+    _same_bits(K2, M2, ref)
+    # graph: captured once, replayed with other coefficients in the same buffers
+    tabs = batch.tables(nodes, coeff, K, M)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        batch.assemble_tables(tabs, stream=s)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            batch.assemble_tables(tabs, stream=s)
+    torch.cuda.synchronize()
+    for seed in (3, 4):
+        for i, (nd, el, _) in enumerate(meshes):
+            coeff[i].copy_(torch.from_numpy(mg.log_uniform_coeff(100 * seed + i, el.shape[0])))
+        for k in K + M:
+            k.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        want = []
+        for i, (nd, el, _) in enumerate(meshes):
+            plan = ef.Plan(NED1, 3, nd.shape[0], elems[i])
+            k, m = plan.assemble(nodes[i], coeff[i])
+            want.append((k.clone(), m.clone()))
+            plan.close()
+        batch.check()
+        _same_bits(K, M, want)
+    with pytest.raises(ef.EdgeFemError):
+        bad = batch.tables(nodes, coeff, K, M)
+        bad[2][0] = None                            # a NULL K for a non-empty mesh
+        batch.assemble_tables(bad)
+    batch.close()

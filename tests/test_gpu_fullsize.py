@@ -3,20 +3,23 @@
 3D Nedelec 64^3 (1,572,864 tets), 3D RT0 128^3 (12,582,912 tets) and 3D
 Nedelec 96^3 (5,308,416 tets), jittered +-0.2h, coefficient log-uniform in
 [0.1, 10]: topology and CSR pattern bit for bit, K and M within 1e-12 of
-max(|oracle|, sum |contributions|), through the same ef_assemble launch the
-benchmark times, against the full oracle (about 12 s, 80 s and 50 s on one
+max(|oracle|, sum |contributions|, sqrt(A_ii A_jj)) and, on every entry not
+small by cancellation, within a plain relative 1e-12 (tests/_parity.py),
+through the same ef_assemble launch the benchmark times, against the full oracle (about 12 s, 80 s and 50 s on one
 core). The benchmark's batch (256 meshes): sampled meshes against the
 oracle. The benchmark's adjoint (96^3): size-independent identities and
 sampled per-element coefficient gradients and per-node coordinate gradients
 against the oracle.
 """
 import gc
+import json
+import os
 
 import numpy as np
 import pytest
 
 from paper_1409_4618_gb300 import meshgen as mg
-from tests._parity import compare, run_gpu
+from tests._parity import compare, run_gpu, worst_entries
 
 pytestmark = pytest.mark.gpu
 
@@ -32,6 +35,13 @@ def test_fullsize_parity(ora, name, kind, n, seed):
     o = ora.assemble(kind, 3, nodes, elems, coeff)
     stats = compare(g, o)
     print(name, stats)
+    # EF_PARITY_STATS=<file>: append the statistics and the worst entries as one JSON line
+    path = os.environ.get("EF_PARITY_STATS")
+    if path:
+        rec = {"case": name, "stats": stats,
+               "worst": {key: worst_entries(g, o, nodes, elems, key) for key in ("K", "M")}}
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
     del g, o
     gc.collect()
 
@@ -133,7 +143,7 @@ def test_fullsize_adjoint_properties_and_sampled_coefficient_gradient(ora):
             ok = np.searchsorted(full_keys, ot["dof2nodes"][:, 0].astype(np.int64) * V + ot["dof2nodes"][:, 1])
             _, g1, _ = ora.adjoint(NED1, 3, nodes, one, coeff[star[k:k + 1]], u[ok], v[ok])
             scale += np.abs(g1[i])
-        assert np.all(np.abs(gxn[i] - gxo[i]) <= 1e-12 * scale.max() * len(star)), (i, gxn[i], gxo[i], scale)
+        assert np.all(np.abs(gxn[i] - gxo[i]) <= 1e-11 * scale), (i, gxn[i], gxo[i], scale)
     # sampled elements: dJ/dsigma_e from the oracle's local matrices and signs
     topo = ora.topology(NED1, 3, nodes, elems)
     gsn = gs.cpu().numpy()
