@@ -17,14 +17,17 @@ import numpy as np
 TOL = 1e-12
 
 # Plain relative error |gpu - oracle| / |oracle| is asserted <= TOL on every
-# entry with |oracle_ij| >= REL_FLOOR * sqrt(A_ii A_jj). Below that the entry
-# is small by cancellation between (or inside) element contributions, and
-# both sides' rounding errors, a few eps * sqrt(A_ii A_jj), are no longer
-# small against it; there the scaled bound above is the one that holds.
-REL_FLOOR = 1e-3
+# entry with |oracle_ij| >= REL_FLOOR * sqrt(A_ii A_jj). The scaled error
+# above stays below 4e-15 on every workload, so there the plain relative
+# error is at most 4e-15 / REL_FLOOR = 4e-13. Below the floor the entry is
+# small by cancellation between (or inside) element contributions, and both
+# sides' rounding errors, a few eps * sqrt(A_ii A_jj), are no longer small
+# against it (measured: up to 1.1e-12 between 1e-3 and 1e-2, up to 3e-9 at
+# 1e-6); there the scaled bound is the one that holds.
+REL_FLOOR = 1e-2
 
 # bands of |oracle_ij| / sqrt(A_ii A_jj) for the recorded error distribution
-BANDS = (1e-3, 1e-6, 1e-9, 1e-12)
+BANDS = (1e-2, 1e-3, 1e-6, 1e-9, 1e-12)
 
 
 def diag_scale(ora: dict, key: str) -> np.ndarray:
