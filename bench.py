@@ -827,6 +827,8 @@ def run_gpu(args):
     tuned = None
     if path.startswith("blocked"):
         plan.set_block(int(path[len("blocked"):]))
+    elif path.startswith("fused"):
+        plan.set_fused(tn, int(path[len("fused"):]))
     elif path == "default":
         tuned = plan.tune(tn, tc, K, M, reps=5)      # library autotuner: pipeline chunks / element-block
 
@@ -981,7 +983,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--path", default="default", choices=["default", "two_pass", "blocked128", "blocked256"])
+    ap.add_argument("--path", default="default",
+                    choices=["default", "two_pass", "blocked128", "blocked256", "fused128", "fused256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")

@@ -97,20 +97,36 @@ typedef struct {
     int32_t assemble_launches;    /* kernel launches made by one ef_assemble */
     int32_t fused_block;          /* elements per CTA of the element-block path if selected, else 0 */
     int64_t fused_blocks;
-    int64_t fused_partial;        /* element-block path: contributions summed by the fix-up */
+    int64_t fused_partial;        /* element-block path: contributions of nonzeros split across blocks */
     int32_t pipeline_chunks;      /* element chunks of the work order (the persistent queue's chunks) */
+    int32_t fused_sfc;            /* element-block path along the Morton order of the centroids (1) or not */
 } ef_plan_info_t;
 int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info);
 
 /* Select how ef_assemble runs. block = 0: leave the element-block path
  * (back to the two-pass kernels or the queue selected before). block = 128
- * or 256: the element-block path, one CTA per block of
- * `block` elements that keeps its local matrices in shared memory, completes
- * the nonzeros lying wholly in the block and hands the others to a fix-up
- * kernel. Results are identical bit for bit (same summation order); only
- * speed differs. Synchronises `stream` and allocates when building the
- * block schedule. Errors: EF_ERR_ARG, EF_ERR_OOM. */
+ * or 256: the element-block path, ONE kernel with one CTA per block of
+ * `block` consecutive elements of the mesh's order: the CTA keeps its
+ * elements' local matrices in shared memory and completes the nonzeros lying
+ * wholly in the block; the contributions of nonzeros split across blocks go
+ * to the plan's scratch, and the CTA that contributes last to such a nonzero
+ * (an integer ticket per nonzero; nothing waits) sums it. Results are
+ * identical bit for bit (every nonzero is summed in ascending element order);
+ * only speed differs. Synchronises `stream` and allocates when building the
+ * block schedule. Errors: EF_ERR_ARG, EF_ERR_OOM, EF_ERR_SIZE (a block's
+ * schedule does not fit in shared memory). */
 int ef_plan_set_block(ef_plan* plan, int block, void* stream);
+
+/* The element-block path of ef_plan_set_block with the blocks taken along a
+ * space-filling (Morton, Z-order) curve through the element centroids under
+ * the coordinates d_nodes (n_nodes x dim, device), so that a block is a
+ * compact piece of the mesh and fewer nonzeros are split across blocks. The
+ * coordinates only choose the grouping: later ef_assemble calls may pass
+ * any coordinates, and the values are those of ef_assemble_two_pass bit for
+ * bit (each nonzero is still summed in ascending element id). block = 0
+ * leaves the element-block path. Synchronises `stream`; allocates.
+ * Errors as ef_plan_set_block. */
+int ef_plan_set_fused(ef_plan* plan, const double* d_nodes, int block, void* stream);
 
 /* Select the one-launch persistent queue with `chunks` element chunks (1 to
  * 16; sums of a chunk may start once the chunks they depend on are done).
@@ -135,7 +151,9 @@ int ef_plan_inject_stall(ef_plan* plan, int on, void* stream);
  * kernels (*chosen = 0); the one-launch persistent queue with 4, 8 or 16
  * element chunks, 128 or 256 elements per tile, 1024 or 4096 nonzeros per
  * sum tile and 0, 1 or 2 element-only CTAs per four (*chosen = chunks*100 +
- * elem_ctas*10 + (tile == 256)); the element-block path (*chosen = -block).
+ * elem_ctas*10 + (tile == 256)); the element-block path in mesh order
+ * (*chosen = -block) and along the Morton curve of the centroids under
+ * d_nodes (*chosen = -(block + 1)).
  * A candidate whose schedule cannot be built (EF_ERR_OOM, EF_ERR_SIZE) is
  * skipped. Overwrites d_Kval / d_Mval. Synchronises `stream`. */
 int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, double* d_Kval, double* d_Mval,
@@ -148,8 +166,8 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
  * and frees the events). ef_plan_profile_read waits for the recorded events
  * and returns the summed milliseconds of the first kernel (the element kernel
  * of the two-pass schedule, the fused kernel of the element-block one, the
- * whole launch of the persistent queue) and of the second (the sum, the
- * fix-up, 0), and the number of calls recorded. Either output may be NULL.
+ * whole launch of the persistent queue or of the element-block kernel) and of
+ * the second (the sum, or 0), and the number of calls recorded. Either output may be NULL.
  * Errors: EF_ERR_ARG, EF_ERR_CUDA. */
 int ef_plan_profile(ef_plan* plan, int max_calls);
 int ef_plan_profile_read(const ef_plan* plan, double* ms_first, double* ms_second, int* calls);
@@ -461,7 +479,7 @@ void ef_csr_free(ef_csr* csr);
  * stream of FP64 additions, multiplications and fused multiply-adds, see
  * Sec. 2.4's local matrices). op = 0: DFMA, 1: DADD, 2: DMUL. Every thread
  * of a grid of 4 CTAs of 256 threads per SM runs 8 independent chains of
- * `iters` operations; *ops_per_s receives the lane operations per second
+ * `iters` operations (rounded up to a multiple of 8); *ops_per_s receives the lane operations per second
  * (one per DFMA), *ms (may be NULL) the timed launch's duration. d_sink: one
  * device double the kernel may write (it never does for these inputs).
  * Launches a short warm-up and the timed kernel on `stream`, synchronises it.

@@ -14,10 +14,10 @@ namespace {
 
 void free_plan_memory(ef_plan* p)
 {
+    release_fused(p);
     void* ptrs[] = {p->d_elems,     p->d_elem2dof,   p->d_signbits,  p->d_dof2nodes,   p->d_rowptr,
                     p->d_colidx,    p->d_seg,        p->d_perm,      p->d_pos_up,      p->d_pos_lo,
-                    p->d_local,     p->d_status,     p->d_fb_slot_off, p->d_fb_sinfo, p->d_fb_cidx,
-                    p->d_fb_posA,   p->d_fb_posB,    p->d_px_uid,
+                    p->d_local,     p->d_status,
                     p->d_stage_nodes, p->d_stage_coeff, p->d_stage_K, p->d_stage_M,
                     p->d_node_off,  p->d_node_inc,   p->d_adj_part,  p->d_adj_jpart, p->d_l2_part,
                     p->d_dof_off,   p->d_dof_inc,    p->d_load_local};
@@ -231,13 +231,14 @@ int ef_plan_info(const ef_plan* plan, ef_plan_info_t* info)
     if (plan->T == 0)
         info->assemble_launches = 0;
     else if (plan->use_blocked && plan->fb_nblocks > 0)
-        info->assemble_launches = plan->n_px > 0 ? 2 : 1;
+        info->assemble_launches = 1;
     else
         info->assemble_launches = (plan->queue && !plan->use_two_pass) ? 1 : 2;
     info->fused_block = plan->use_blocked ? plan->fb_block : 0;
     info->pipeline_chunks = plan->pc_chunks;
     info->fused_blocks = plan->fb_nblocks;
     info->fused_partial = plan->n_partial;
+    info->fused_sfc = plan->use_blocked ? plan->fb_sfc : 0;
     return EF_OK;
 }
 
@@ -249,7 +250,21 @@ int ef_plan_set_block(ef_plan* plan, int block, void* stream)
         return EF_OK;
     }
     if (!fused_block_supported(block)) return EF_ERR_ARG;
-    EF_TRY(build_fused_block(plan, block, (cudaStream_t)stream));
+    EF_TRY(build_fused_block(plan, block, nullptr, (cudaStream_t)stream));
+    plan->use_blocked = 1;
+    plan->use_two_pass = 0;
+    return EF_OK;
+}
+
+int ef_plan_set_fused(ef_plan* plan, const double* d_nodes, int block, void* stream)
+{
+    if (!plan || (plan->T > 0 && !d_nodes)) return EF_ERR_ARG;
+    if (block == 0) {
+        plan->use_blocked = 0;
+        return EF_OK;
+    }
+    if (!fused_block_supported(block)) return EF_ERR_ARG;
+    EF_TRY(build_fused_block(plan, block, d_nodes, (cudaStream_t)stream));
     plan->use_blocked = 1;
     plan->use_two_pass = 0;
     return EF_OK;
@@ -285,6 +300,7 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
     EF_CUDA(cudaEventCreate(&e1));
     struct Cand {
         int chunks, block, two_pass;   // block > 0: element-block path; two_pass: plain kernels
+        int sfc;                       // element-block path along the Morton order of the centroids
         ef_batch_config_t q;
     };
     std::vector<Cand> cands;
@@ -311,17 +327,19 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
                     if (k.q.ctas_per_sm >= 1) cands.push_back(k);
                 }
     }
-    for (int b : {128, 256}) {
-        Cand k{};
-        k.block = b;
-        cands.push_back(k);
-    }
+    for (int sfc : {0, 1})
+        for (int b : {128, 256}) {
+            Cand k{};
+            k.block = b;
+            k.sfc = sfc;
+            cands.push_back(k);
+        }
     int st = EF_OK, best = -1;
     float best_ms = 1e30f;
     for (size_t i = 0; i < cands.size() && st == EF_OK; i++) {
         const Cand& c = cands[i];
         if (c.block > 0)
-            st = ef_plan_set_block(plan, c.block, stream);
+            st = c.sfc ? ef_plan_set_fused(plan, d_nodes, c.block, stream) : ef_plan_set_block(plan, c.block, stream);
         else if (c.two_pass) {
             // the two-pass kernels do not depend on the chunking; keep the
             // default one, which ef_assemble_host overlaps with its copies
@@ -360,8 +378,8 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
     if (st != EF_OK || best < 0) return st != EF_OK ? st : EF_ERR_ARG;
     const Cand& c = cands[best];
     if (c.block > 0) {
-        st = ef_plan_set_block(plan, c.block, stream);
-        if (chosen) *chosen = -c.block;
+        st = c.sfc ? ef_plan_set_fused(plan, d_nodes, c.block, stream) : ef_plan_set_block(plan, c.block, stream);
+        if (chosen) *chosen = c.sfc ? -(c.block + 1) : -c.block;
     } else if (c.two_pass) {
         st = ef_plan_set_pipeline(plan, c.chunks, stream);
         plan->use_two_pass = 1;

@@ -108,18 +108,25 @@ struct ef_plan {
     double* d_local;      // 2 * np * T: contribution list of the two-pass paths, (K, M) pairs in work order
     int* d_status;        // device status word
 
-    // fused path (blocks of fb_block consecutive elements): see ef_fused.cu
+    // fused path (one kernel over blocks of fb_block elements along an element order): see ef_fused.cu
     int fb_block;             // elements per block (0: no fused schedule)
+    int fb_sfc;               // 1: blocks along the Morton order of the element centroids; 0: mesh order
+    int fb_qcap;              // most partial slots of one block (its ticket queue in shared memory)
     int64_t fb_nblocks;
     int64_t fb_nslots;
+    uint32_t* d_fb_order;     // T: the elements in block order (NULL: mesh order)
     uint32_t* d_fb_slot_off;  // nblocks + 1: slot range of each block
-    uint32_t* d_fb_sinfo;     // per slot: start | count << 16 | partial << 31
-    uint32_t* d_fb_posA;      // per slot: CSR position of (r,c), or first global list position if partial
+    uint32_t* d_fb_part_off;  // nblocks: first partial slot of each block
+    uint32_t* d_fb_sinfo;     // per slot: start | count << 16
+    uint32_t* d_fb_posA;      // per slot: CSR position of (r,c), or the split index if partial
     uint32_t* d_fb_posB;      // per slot: CSR position of (c,r), or 0xffffffff
     uint16_t* d_fb_cidx;      // per contribution, block-major: pair * block + element in block
-    uint32_t* d_px_uid;       // upper nonzeros split across blocks (summed by the fix-up)
+    uint32_t* d_fb_gpos;      // per contribution, block-major: its position in the global list
+    uint32_t* d_px_uid;       // upper nonzeros split across blocks
+    uint32_t* d_px_nb;        // per split nonzero: blocks contributing to it
+    uint32_t* d_px_cnt;       // per split nonzero: tickets drawn in the current call
     int64_t n_px;
-    int64_t n_partial;        // raw contributions of the split nonzeros
+    int64_t n_partial;        // contributions of the split nonzeros
 
     // adjoint (3D Nedelec): node -> (element, vertex) incidence in element order, scratch
     uint32_t* d_node_off;    // V + 1
@@ -160,14 +167,15 @@ int plan_create_internal(int kind, int dim, int64_t n_nodes, int64_t n_elems, co
 int validate_elems(ef_plan* p, cudaStream_t s);
 int build_topology(ef_plan* p, cudaStream_t s);
 int build_pattern(ef_plan* p, cudaStream_t s);
-int build_fused(ef_plan* p, cudaStream_t s);
 int build_work_order(ef_plan* p, int nchunks, cudaStream_t s);
 int default_pipeline_chunks(const ef_plan* p);
 void release_work_order(ef_plan* p);
 // Order a list of upper nonzeros by descending contribution count (stable), in place.
 int order_by_count(const uint32_t* seg, uint32_t* list, int64_t n, uint64_t* keys, uint32_t* vals, void* tmp,
                    cudaStream_t s);
-int build_fused_block(ef_plan* p, int BE, cudaStream_t s);
+// nodes == NULL: blocks in mesh order; else along the Morton order of the centroids under nodes
+int build_fused_block(ef_plan* p, int BE, const double* nodes, cudaStream_t s);
+void release_fused(ef_plan* p);
 bool fused_block_supported(int BE);
 int build_adjoint(ef_plan* p, cudaStream_t s);
 int launch_two_pass(const ef_plan* p, const double* nodes, const double* coeff, double* K, double* M, cudaStream_t s);

@@ -48,7 +48,7 @@ class EdgeFemError(RuntimeError):
 class PlanInfo(C.Structure):
     _fields_ = [("n_dofs", C.c_int64), ("nnz", C.c_int64), ("n_upper", C.c_int64), ("n_contrib", C.c_int64),
                 ("assemble_launches", C.c_int32), ("fused_block", C.c_int32), ("fused_blocks", C.c_int64),
-                ("fused_partial", C.c_int64), ("pipeline_chunks", C.c_int32)]
+                ("fused_partial", C.c_int64), ("pipeline_chunks", C.c_int32), ("fused_sfc", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +90,7 @@ def load():
             "ef_plan_pattern": ([P, P, P, P], I),
             "ef_plan_info": ([P, C.POINTER(PlanInfo)], I),
             "ef_plan_set_block": ([P, I, P], I),
+            "ef_plan_set_fused": ([P, P, I, P], I),
             "ef_plan_set_pipeline": ([P, I, P], I),
             "ef_plan_inject_stall": ([P, I, P], I),
             "ef_plan_tune": ([P, P, P, P, P, I, C.POINTER(C.c_int), P], I),
@@ -349,6 +350,12 @@ class Plan:
     def set_block(self, block: int, stream=None):
         ef_plan_set_block(self.handle, block, stream)
 
+    def set_fused(self, nodes, block: int, stream=None):
+        """Element-block path with blocks along the Morton curve of the centroids under `nodes` (0: leave it)."""
+        self._need(nodes, self.n_nodes * self.dim, "nodes")
+        _check(load().ef_plan_set_fused(self.handle, _dev(nodes, torch.float64, "nodes"), int(block),
+                                        _stream_ptr(stream)))
+
     def set_pipeline(self, chunks: int, stream=None):
         _check(load().ef_plan_set_pipeline(self.handle, int(chunks), _stream_ptr(stream)))
 
@@ -359,7 +366,8 @@ class Plan:
 
     def tune(self, nodes, coeff=None, K=None, M=None, reps: int = 5, stream=None) -> int:
         """Pick the fastest ef_assemble schedule for this plan: 0 (two-pass), chunks*100 + elem_ctas*10 + (tile
-        == 256) (persistent queue) or -block (element-block path)."""
+        == 256) (persistent queue), -block (element-block path in mesh order) or -(block + 1) (element-block path
+        along the Morton curve of the centroids)."""
         self._need_mesh(nodes, coeff, K, M)
         K, M = self._vals(K, M)
         chosen = C.c_int(0)

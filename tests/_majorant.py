@@ -72,9 +72,11 @@ def p1_solution(nodes, elems, xhat, w):
     return np.einsum("ti,tid->td", v[elems], G)
 
 
-def minimise(backend, nodes, elems, iters, n=4):
+def minimise(backend, nodes, elems, iters, n=4, record=None):
     """Algorithm 1 from beta = 1 for `iters` iterations: [(beta, sqrt(M),
-    I_eff)] of each iteration (beta the value used in that iteration)."""
+    I_eff)] of each iteration (beta the value used in that iteration). With a
+    dict `record`, also keeps the backend's quantities (K, M, the two load
+    vectors, the norms and each iteration's y) for comparison."""
     d = nodes.shape[1]
     T = elems.shape[0]
     xhat, w = backend.ref_rule(n)
@@ -88,6 +90,8 @@ def minimise(backend, nodes, elems, iters, n=4):
     b_grad = backend.load_vector(gv, n)                            # int grad v . phi_i
     b_div = backend.load_derivative(np.ascontiguousarray(fx[..., None]), n)   # int f div phi_i
     err_v = backend.norm_l2(np.ascontiguousarray(bubble_gradient(x) - gv), n)  # ||grad (u - v)||^2
+    if record is not None:
+        record.update(K=K, M=M, x=x, gv=gv, fx=fx, b_grad=b_grad, b_div=b_div, err_v=err_v, ys=[], t1=[], t2=[])
     beta = 1.0
     out = []
     for _ in range(iters):
@@ -96,6 +100,10 @@ def minimise(backend, nodes, elems, iters, n=4):
         y = spla.spsolve(A.tocsc(), rhs)
         t1 = backend.norm_l2(gv, n, y)                             # ||grad v - y||^2
         t2 = backend.norm_derivative(np.ascontiguousarray(-fx[..., None]), n, y)   # ||div y + f||^2
+        if record is not None:
+            record["ys"].append(y)
+            record["t1"].append(t1)
+            record["t2"].append(t2)
         Mv = (1.0 + 1.0 / beta) * t1 + (1.0 + beta) * C * C * t2
         out.append((beta, math.sqrt(Mv), math.sqrt(Mv / err_v)))
         beta = math.sqrt(t1) / (C * math.sqrt(t2))

@@ -72,6 +72,10 @@ def run_gpu(kind, dim, nodes, elems, coeff=None, path="default", check=True, coe
         elif path.startswith("blocked"):
             plan.set_block(int(path[len("blocked"):]))
             K, M = plan.assemble(tn, tc)
+        elif path.startswith("fused"):
+            plan.set_fused(tn, int(path[len("fused"):]))
+            K, M = plan.assemble(tn, tc)
+            K, M = plan.assemble(tn, tc, K, M)        # a second call: the tickets were reset by the first
         elif path.startswith("chunks"):
             plan.set_pipeline(int(path[len("chunks"):]))
             K, M = plan.assemble(tn, tc)

@@ -6,8 +6,9 @@ tests/_parity.py. Sizes span many 256-element tiles with ragged tails; local
 node order and element order are shuffled so that det B_K takes both signs;
 edge cases: one element, no element, unused nodes, the L-shaped domain. Every
 assembly schedule (the default two-pass kernels, the one-launch persistent
-queue, element-block with 128 or 256 elements per CTA) is checked, and the
-default path also inside a CUDA graph.
+queue, element-block with 128 or 256 elements per CTA in mesh order or along
+the Morton curve of the centroids) is checked, and the default path also
+inside a CUDA graph.
 """
 import numpy as np
 import pytest
@@ -59,7 +60,7 @@ CASES = ["c1_rt2d_32", "ned2d_33_shuffled", "rt2d_37_shuffled", "ned3d_8", "ned3
 
 
 @pytest.mark.parametrize("name", CASES)
-@pytest.mark.parametrize("path", ["default", "chunks4", "blocked128", "blocked256"])
+@pytest.mark.parametrize("path", ["default", "chunks4", "blocked128", "blocked256", "fused128", "fused256"])
 def test_parity(ora, name, path):
     kind, dim, nodes, elems, coeff = _case(name)
     o = ora.assemble(kind, dim, nodes, elems, coeff)
@@ -89,13 +90,15 @@ def test_empty_mesh(kind, dim):
 @pytest.mark.parametrize("kind", [NED1, RT0])
 def test_paths_agree_bitwise_and_runs_repeat(ora, kind):
     """The persistent queue (several element chunks at 131,712 tets), the plain
-    two-pass and the element-block paths form the same sums in the same order:
+    two-pass and the element-block paths (mesh order and Morton order) form the
+    same sums in the same order:
     identical bits, run after run; and the queue's result passes parity."""
     nodes, elems = mg.kuhn_cube(28, 0.2, 12)
     coeff = mg.log_uniform_coeff(12, elems.shape[0])
     a = run_gpu(kind, 3, nodes, elems, coeff, path="chunks3")
     others = [run_gpu(kind, 3, nodes, elems, coeff, path=p)
-              for p in ("default", "two_pass", "chunks3", "chunks16", "blocked128", "blocked256")]
+              for p in ("default", "two_pass", "chunks3", "chunks16", "blocked128", "blocked256", "fused128",
+                        "fused256")]
     for key in ("K", "M"):
         for other in others:
             assert np.array_equal(a[key].view(np.uint64), other[key].view(np.uint64))
@@ -365,4 +368,51 @@ def test_fig3_shared_edge_signs_gpu(kind):
     assert ((sb[0] >> kn) & 1) == (0 if ex["K_n_sign"] > 0 else 1)
     assert ((sb[1] >> km) & 1) == (0 if ex["K_m_sign"] > 0 else 1)
     assert e2d[0][kn] == e2d[1][km]
+    plan.close()
+
+
+def test_fused_order_from_other_coordinates_and_graph():
+    """The Morton grouping of ef_plan_set_fused comes from one set of
+    coordinates; assembling with other coordinates and coefficients still
+    gives the two-pass bits, call after call and from a CUDA graph (the split
+    nonzeros' tickets reset themselves)."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    nodes, elems = mg.kuhn_cube(17, 0.2, 31)
+    elems = mg.shuffle_local_order(elems, 31)
+    perm = np.argsort(mg.uniform(31, 11, np.arange(elems.shape[0])))
+    elems = elems[perm]
+    dev = torch.device("cuda")
+    plan = ef.Plan(NED1, 3, nodes.shape[0], torch.from_numpy(elems).to(dev))
+    other, _ = mg.kuhn_cube(17, 0.2, 32)
+    plan.set_fused(torch.from_numpy(other * 3.0 + 1.0).to(dev), 128)
+    info = plan.info()
+    assert info["fused_sfc"] == 1 and info["assemble_launches"] == 1 and info["fused_block"] == 128
+    tn = torch.from_numpy(nodes).to(dev)
+    for seed in (1, 2):
+        tc = torch.from_numpy(mg.log_uniform_coeff(seed, elems.shape[0])).to(dev)
+        K0, M0 = plan.assemble_two_pass(tn, tc)
+        for _ in range(2):
+            K, M = plan.assemble(tn, tc)
+            assert torch.equal(K.view(torch.int64), K0.view(torch.int64))
+            assert torch.equal(M.view(torch.int64), M0.view(torch.int64))
+    K = torch.full_like(K0, float("nan"))
+    M = torch.full_like(M0, float("nan"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        plan.assemble(tn, tc, K, M, stream=s)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            plan.assemble(tn, tc, K, M, stream=s)
+    for _ in range(3):
+        K.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(K.view(torch.int64), K0.view(torch.int64))
+        assert torch.equal(M.view(torch.int64), M0.view(torch.int64))
+    plan.check()
     plan.close()
