@@ -161,10 +161,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-# FP64 instructions per tetrahedron of the Nedelec-3D element kernel as
-# executed (ncu sass counters of one launch on the 48^3 cube, divided by its
-# elements): DADD, DFMA, DMUL.
-ELEMENT_KERNEL_FP64_MIX = {"dadd": 54, "dfma": 46, "dmul": 32}
+# FP64 instructions per element of each element kernel as executed (ncu
+# sm__sass_thread_inst_executed_op_{dadd,dfma,dmul}_pred_on.sum of one launch
+# divided by its elements; every FP64 warp instruction had all 32 lanes on):
+# (kind, dim) -> DADD, DFMA, DMUL. Measured on the 24^3 cube (3D) and the
+# level-5 L-shape (2D); the counts do not depend on the mesh.
+ELEMENT_KERNEL_FP64_EXECUTED = {
+    (2, 3): {"dadd": 54, "dfma": 46, "dmul": 32},
+    (1, 3): {"dadd": 21, "dfma": 37, "dmul": 17},
+    (1, 2): {"dadd": 10, "dfma": 18, "dmul": 10},
+    (2, 2): {"dadd": 18, "dfma": 18, "dmul": 9},
+}
+ELEMENT_KERNEL_FP64_MIX = ELEMENT_KERNEL_FP64_EXECUTED[(2, 3)]
+
+
+def fp64_executed_per_element(kind: int, dim: int) -> int:
+    return sum(ELEMENT_KERNEL_FP64_EXECUTED[(kind, dim)].values())
 FP64_PROBE_ITERS = 100_000
 
 
@@ -412,6 +424,17 @@ def run_batched(args, dev, plain_rate):
     return out
 
 
+def _fp64_leg(kind: int, dim: int, T: int, ms: float) -> dict:
+    """An element kernel's launch against the FP64 pipe peak: by the source
+    count (the algorithmic operations) and by the executed instructions."""
+    src, exe = fp64_ops_per_element(kind, dim), fp64_executed_per_element(kind, dim)
+    peak = FP64_PEAK["T_ops_per_s"]
+    a_src, a_exe = src * T / (ms / 1e3) / 1e12, exe * T / (ms / 1e3) / 1e12
+    return {"ops_per_elem": src, "achieved": a_src, "peak": peak, "unit": "T fp64-ops/s", "frac": a_src / peak,
+            "executed_per_elem": exe, "achieved_executed": a_exe, "frac_executed": a_exe / peak,
+            "ms_per_launch": ms, "peak_source": FP64_PEAK["source"]}
+
+
 def run_rt0(args, dev, peaks):
     """The two RT0 workloads: 3D RT0 on the 128^3 cube (12,582,912 tets,
     jitter 0.2h seed 3, log-uniform coefficient; the large, memory-heavy case)
@@ -423,7 +446,8 @@ def run_rt0(args, dev, peaks):
     from paper_1409_4618_gb300 import edgefem as ef
 
     out = {}
-    for name, dim, n, jitter, seed, unit in (("rt0_3d_kuhn128_jitter0.2", 3, 128, 0.2, 3, False),
+    for name, dim, n, jitter, seed, unit in ((f"rt0_3d_kuhn{args.rt0_cube}_jitter0.2", 3, args.rt0_cube, 0.2, 3,
+                                              False),
                                              ("rt0_2d_square32", 2, 32, 0.0, 0, True)):
         if dim == 3:
             nodes, elems = mg.kuhn_cube(n, jitter, seed)
@@ -462,12 +486,7 @@ def run_rt0(args, dev, peaks):
                              "algorithmic_bytes_per_step": int(alg), "bytes_per_elem": alg / T}}
         if tuned == 0 and calls:
             # the element kernel of the two-pass schedule against the FP64 pipe
-            ops = fp64_ops_per_element(1, dim) * T
-            ach = ops / (k1 / calls / 1e3) / 1e12
-            out[name]["fp64_element_kernel"] = {"ops_per_elem": fp64_ops_per_element(1, dim), "achieved": ach,
-                                                "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-ops/s",
-                                                "frac": ach / FP64_PEAK["T_ops_per_s"],
-                                                "peak_source": FP64_PEAK["source"]}
+            out[name]["fp64_element_kernel"] = _fp64_leg(1, dim, T, k1 / calls)
         plan.close()
         del K, M
         torch.cuda.empty_cache()
@@ -521,12 +540,7 @@ def run_lshape(args, dev, peaks):
                "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                        "algorithmic_bytes_per_step": int(alg), "bytes_per_elem": alg / T}}
         if tuned == 0 and calls:
-            ops = fp64_ops_per_element(kind, 2) * T
-            ach = ops / (k1 / calls / 1e3) / 1e12
-            leg["fp64_element_kernel"] = {"ops_per_elem": fp64_ops_per_element(kind, 2), "achieved": ach,
-                                          "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-ops/s",
-                                          "frac": ach / FP64_PEAK["T_ops_per_s"],
-                                          "peak_source": FP64_PEAK["source"]}
+            leg["fp64_element_kernel"] = _fp64_leg(kind, 2, T, k1 / calls)
         out[name] = leg
         plan.close()
         del K, M
@@ -804,8 +818,12 @@ def run_gpu(args):
 
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    probe = run_fp64_probe(local)
-    FP64_PEAK.update(T_ops_per_s=probe["peak_T_ops_per_s"], source="measured (bench fp64 leg: ef_fp64_probe DFMA)")
+    if args.no_fp64_probe:
+        probe = {"peak_T_ops_per_s": FP64_PEAK_TOPS, "element_mix_T_ops_per_s": FP64_PEAK_TOPS,
+                 "clocks": {"sm_mhz": None}, "skipped": "--no-fp64-probe (nominal peak)"}
+    else:
+        probe = run_fp64_probe(local)
+        FP64_PEAK.update(T_ops_per_s=probe["peak_T_ops_per_s"], source="measured (bench fp64 leg: ef_fp64_probe DFMA)")
     nodes, elems, coeff = _workload()
     w = WORKLOAD
     tn = torch.from_numpy(nodes).to(dev)
@@ -924,15 +942,16 @@ def run_gpu(args):
     roofline = {
         "bound": "alu", "unit": "T fp64-ops/s", "achieved": achieved_ops, "peak": peak,
         "frac": achieved_ops / peak, "traffic": traffic,
-        "peak_source": "measured (bench fp64 leg: ef_fp64_probe DFMA lane-ops/s on this GPU, "
-                       f"median SM clock {probe['clocks'].get('sm_mhz')} MHz during the probe)",
+        "peak_source": ("measured (bench fp64 leg: ef_fp64_probe DFMA lane-ops/s on this GPU, "
+                        f"median SM clock {probe['clocks'].get('sm_mhz')} MHz during the probe)"
+                        if "skipped" not in probe else "nominal (" + probe["skipped"] + ")"),
         "peak_nominal": FP64_PEAK_TOPS,
         "peak_nominal_source": f"{SMS} SMs x {FP64_PER_CLK_PER_SM} FP64 ops/clk/SM x {SM_MAX_MHZ} MHz",
         "kernel": dom_name, "ms_per_launch": dom_ms,
         "fp64_ops_per_launch": int(dom_ops), "fp64_ops_per_elem": dom_ops / T,
         "fp64_ops_source": "counted from the source (csrc/ef_element.cuh)",
         "executed": (None if exec_ops is None else
-                     {"fp64_ops_per_elem": exec_ops / T, "source": "ncu sass FP64 instruction counters, 48^3",
+                     {"fp64_ops_per_elem": exec_ops / T, "source": "ncu sass FP64 instruction counters",
                       "achieved": exec_ops / (dom_ms / 1e3) / 1e12,
                       "frac": exec_ops / (dom_ms / 1e3) / 1e12 / peak,
                       "frac_of_mix_peak": exec_ops / (dom_ms / 1e3) / 1e12 / probe["element_mix_T_ops_per_s"]}),
@@ -1002,6 +1021,9 @@ def main():
     ap.add_argument("--lshape-level", type=int, default=11,
                     help="level of the 2D L-shaped workload (6 4^L triangles)")
     ap.add_argument("--rt0-steps", type=int, default=20)
+    ap.add_argument("--rt0-cube", type=int, default=128, help="cubes per axis of the 3D RT0 workload")
+    ap.add_argument("--no-fp64-probe", action="store_true",
+                    help="skip the FP64 throughput probe (profiling runs); rooflines then use the nominal peak")
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-batch-baselines", action="store_true",

@@ -69,20 +69,22 @@ def test_parity(ora, name, path):
 
 
 @pytest.mark.parametrize("kind,dim", [(RT0, 2), (NED1, 2), (RT0, 3), (NED1, 3)])
-def test_single_element_and_unused_nodes(ora, kind, dim):
+@pytest.mark.parametrize("path", ["default", "blocked128", "fused256"])
+def test_single_element_and_unused_nodes(ora, kind, dim, path):
     rng = np.random.default_rng(5)
     nodes = rng.random((9, dim))
     elems = np.array([[7, 2, 5] + ([1] if dim == 3 else [])], dtype=np.int32)
     o = ora.assemble(kind, dim, nodes, elems, np.array([2.5]))
-    g = run_gpu(kind, dim, nodes, elems, np.array([2.5]))
+    g = run_gpu(kind, dim, nodes, elems, np.array([2.5]), path=path)
     compare(g, o)
 
 
 @pytest.mark.parametrize("kind,dim", [(RT0, 2), (NED1, 3)])
-def test_empty_mesh(kind, dim):
+@pytest.mark.parametrize("path", ["default", "fused128"])
+def test_empty_mesh(kind, dim, path):
     nodes = np.zeros((4, dim))
     elems = np.zeros((0, dim + 1), dtype=np.int32)
-    g = run_gpu(kind, dim, nodes, elems)
+    g = run_gpu(kind, dim, nodes, elems, path=path)
     assert g["n_dofs"] == 0 and g["nnz"] == 0
     np.testing.assert_array_equal(g["rowptr"], [0])
 
