@@ -429,6 +429,7 @@ int ef_assemble(const ef_plan* plan, const double* d_nodes, const double* d_coef
                 void* stream)
 {
     EF_TRY(assemble_checks(plan, d_nodes, d_Kval, d_Mval));
+    if (plan->T == 0) return EF_OK;   // no elements: no nonzeros either
     cudaStream_t s = (cudaStream_t)stream;
     profile_begin(plan, s);
     int st;
