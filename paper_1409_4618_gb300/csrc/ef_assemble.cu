@@ -24,8 +24,6 @@
 // The chunking of the work order (the chunk that completes each nonzero) is
 // what the persistent queue of ef_queue.cu interleaves; the kernels here are
 // the plain two-pass form (ef_assemble_two_pass).
-#include <type_traits>
-
 #include "ef_assemble.cuh"
 #include "ef_internal.cuh"
 #include "ef_queue.cuh"
@@ -136,65 +134,8 @@ __global__ void k_work_inv(const uint32_t* order, int64_t U, const uint32_t* seg
     for (uint32_t s = s0; s < s1; s++) inv[perm[s]] = w0 + (s - s0);
 }
 
-// Work item i sums list[wseg[i] .. wseg[i+1]): the contributions of one upper
-// nonzero, contiguous and in ascending element order; consecutive items are
-// consecutive in the list, so a warp reads one contiguous run. The items are
-// summed in the work order (descending count inside windows, so a warp's
-// loops have equal length) but stored in position order: a CTA owns the
-// aligned block of SB work items [SB b, SB b + SB) (only those in [w0, w1)
-// on this launch), keeps its sums in shared memory, and thread t then writes
-// the t-th item of the block in ascending (r, c) position, and again in
-// ascending (c, r) position (the plan's store orders). Stores of a warp then
-// fall on few, mostly adjacent sectors instead of 32 scattered ones;
-// scattered 8-byte stores are bound by the L2's transaction rate.
-constexpr int SB = 256;
-using StoreIdx = std::conditional_t<(SB <= 256), uint8_t, uint16_t>;
-
-// Sums of the aligned block [base, base + SB) of work items, those in
-// [w0, w1) only, stored in position order.
-__device__ __forceinline__ void scatter_body(int64_t base, int64_t w0, int64_t w1, int64_t U,
-                                             const uint32_t* __restrict__ wseg, const uint32_t* __restrict__ wpos_up,
-                                             const uint32_t* __restrict__ wpos_lo,
-                                             const StoreIdx* __restrict__ st_up, const StoreIdx* __restrict__ st_lo,
-                                             const double2* __restrict__ list, double* __restrict__ K,
-                                             double* __restrict__ M)
-{
-    __shared__ double sk[SB], sm[SB];
-    __shared__ uint32_t su[SB], sl[SB];
-    const int t = threadIdx.x;
-    const int64_t i = base + t;
-    if (i >= w0 && i < w1) {
-        const uint32_t s0 = wseg[i], s1 = wseg[i + 1];
-        su[t] = wpos_up[i];
-        sl[t] = wpos_lo[i];
-        double2 v = list[s0];
-        double k = v.x, m = v.y;
-        for (uint32_t s = s0 + 1; s < s1; s++) {
-            v = list[s];
-            k += v.x;
-            m += v.y;
-        }
-        sk[t] = k;
-        sm[t] = m;
-    }
-    __syncthreads();
-    if (base + t >= U) return;
-    int q = st_up[base + t];
-    if (base + q >= w0 && base + q < w1) {
-        const uint32_t p = su[q];
-        K[p] = sk[q];
-        M[p] = sm[q];
-    }
-    q = st_lo[base + t];
-    if (base + q >= w0 && base + q < w1) {
-        const uint32_t p = sl[q];
-        if (p != 0xffffffffu) {
-            K[p] = sk[q];
-            M[p] = sm[q];
-        }
-    }
-}
-
+// The sum kernels: one CTA of SB threads per aligned block of SB work items
+// (sum_block of ef_assemble.cuh).
 __global__ void __launch_bounds__(SB) k_scatter(int64_t w0, int64_t w1, int64_t U, const uint32_t* __restrict__ wseg,
                                                 const uint32_t* __restrict__ wpos_up,
                                                 const uint32_t* __restrict__ wpos_lo,
@@ -202,7 +143,7 @@ __global__ void __launch_bounds__(SB) k_scatter(int64_t w0, int64_t w1, int64_t 
                                                 const double2* __restrict__ list, double* __restrict__ K,
                                                 double* __restrict__ M)
 {
-    scatter_body((w0 / SB + blockIdx.x) * SB, w0, w1, U, wseg, wpos_up, wpos_lo, st_up, st_lo, list, K, M);
+    sum_block<SB, false>((w0 / SB + blockIdx.x) * SB, w0, w1, U, wseg, wpos_up, wpos_lo, st_up, st_lo, list, K, M);
 }
 
 // The sum over every mesh of a batch: CTA b takes the SB-block of work items
@@ -217,8 +158,8 @@ __global__ void __launch_bounds__(SB, 8) k_batch_scatter(const QueueMesh* __rest
     __shared__ QueueMesh d;
     __shared__ int64_t first;
     const int64_t base = load_block_mesh(md, blk_mesh, blk_off, d, &first) * SB;
-    scatter_body(base, 0, d.U, d.U, d.wseg, d.wpos_up, d.wpos_lo, (const StoreIdx*)d.wst_up,
-                 (const StoreIdx*)d.wst_lo, d.list, d.K, d.M);
+    sum_block<SB, false>(base, 0, d.U, d.U, d.wseg, d.wpos_up, d.wpos_lo, (const StoreIdx*)d.wst_up,
+                  (const StoreIdx*)d.wst_lo, d.list, d.K, d.M);
 }
 
 // Store-order keys: block of the work item, then its CSR position.
