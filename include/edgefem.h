@@ -146,8 +146,9 @@ int ef_plan_set_pipeline(ef_plan* plan, int chunks, void* stream);
  * 0) if another schedule is selected. */
 int ef_plan_inject_stall(ef_plan* plan, int on, void* stream);
 
-/* Autotuner for ef_assemble on this plan: times `reps` calls of each
- * candidate on the given buffers and keeps the fastest: the plain two-pass
+/* Autotuner for ef_assemble on this plan: times at least `reps` calls of each
+ * candidate (and enough calls for about 2 ms) on the given buffers and keeps
+ * the fastest: the plain two-pass
  * kernels (*chosen = 0); the one-launch persistent queue with 4, 8 or 16
  * element chunks, 128 or 256 elements per tile, 1024 or 4096 nonzeros per
  * sum tile and 0, 1 or 2 element-only CTAs per four (*chosen = chunks*100 +

@@ -359,8 +359,21 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
         }
         if (st != EF_OK) break;
         if ((st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream)) != EF_OK) break;
+        // one timed call sets how many to time: at least `reps`, and enough for
+        // about 2 ms, so that calls of a few microseconds are not timed by noise
         cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && st == EF_OK; r++) st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream);
+        st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream);
+        cudaEventRecord(e1, s);
+        float one = 0;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&one, e0, e1) != cudaSuccess) {
+            st = EF_ERR_CUDA;
+            break;
+        }
+        int n = reps;
+        if (one > 0 && one * n < 2.0f) n = (int)(2.0f / one) + 1;
+        if (n > 1000) n = 1000;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < n && st == EF_OK; r++) st = ef_assemble(plan, d_nodes, d_coeff, d_Kval, d_Mval, stream);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             st = EF_ERR_CUDA;
@@ -368,6 +381,7 @@ int ef_plan_tune(ef_plan* plan, const double* d_nodes, const double* d_coeff, do
         }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
+        ms /= n;
         if (ms < best_ms) {
             best_ms = ms;
             best = (int)i;

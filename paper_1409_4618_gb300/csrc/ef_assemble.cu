@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(SB) k_scatter(int64_t w0, int64_t w1, int64_t 
                                                 const double2* __restrict__ list, double* __restrict__ K,
                                                 double* __restrict__ M)
 {
-    sum_block<SB, false>((w0 / SB + blockIdx.x) * SB, w0, w1, U, wseg, wpos_up, wpos_lo, st_up, st_lo, list, K, M);
+    sum_block((w0 / SB + blockIdx.x) * SB, w0, w1, U, wseg, wpos_up, wpos_lo, st_up, st_lo, list, K, M);
 }
 
 // The sum over every mesh of a batch: CTA b takes the SB-block of work items
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(SB, 8) k_batch_scatter(const QueueMesh* __rest
     __shared__ QueueMesh d;
     __shared__ int64_t first;
     const int64_t base = load_block_mesh(md, blk_mesh, blk_off, d, &first) * SB;
-    sum_block<SB, false>(base, 0, d.U, d.U, d.wseg, d.wpos_up, d.wpos_lo, (const StoreIdx*)d.wst_up,
+    sum_block(base, 0, d.U, d.U, d.wseg, d.wpos_up, d.wpos_lo, (const StoreIdx*)d.wst_up,
                   (const StoreIdx*)d.wst_lo, d.list, d.K, d.M);
 }
 

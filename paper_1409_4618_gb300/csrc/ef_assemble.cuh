@@ -70,34 +70,29 @@ __device__ __forceinline__ bool compute_element(const int32_t* __restrict__ elem
 // ascending (r, c) and in ascending (c, r) CSR position (the plan's per-block
 // store orders st_up, st_lo: the t-th entry is the block-local item stored
 // t-th), so that the stores of a warp fall on few adjacent sectors; scattered
-// 8-byte stores are bound by the L2's transaction rate. NT threads share a
-// block (NT divides SB). COHERENT: the list was written by other CTAs of the
-// same launch (read it through L2 only, never the read-only path).
+// 8-byte stores are bound by the L2's transaction rate.
 constexpr int SB = 256;
 using StoreIdx = uint8_t;
 
-template <int NT, bool COHERENT>
 __device__ __forceinline__ void sum_block(int64_t base, int64_t w0, int64_t w1, int64_t U,
                                           const uint32_t* __restrict__ wseg, const uint32_t* __restrict__ wpos_up,
                                           const uint32_t* __restrict__ wpos_lo, const StoreIdx* __restrict__ st_up,
                                           const StoreIdx* __restrict__ st_lo, const double2* __restrict__ list,
                                           double* __restrict__ K, double* __restrict__ M)
 {
-    static_assert(SB % NT == 0, "threads must divide the block");
     __shared__ double sk[SB], sm[SB];
     __shared__ uint32_t su[SB], sl[SB];
-#pragma unroll
-    for (int r = 0; r < SB / NT; r++) {
-        const int t = threadIdx.x + r * NT;
+    const int t = threadIdx.x;
+    {
         const int64_t i = base + t;
         if (i >= w0 && i < w1) {
             const uint32_t s0 = wseg[i], s1 = wseg[i + 1];
             su[t] = wpos_up[i];
             sl[t] = wpos_lo[i];
-            double2 v = COHERENT ? __ldcg(list + s0) : list[s0];
+            double2 v = list[s0];
             double k = v.x, m = v.y;
             for (uint32_t s = s0 + 1; s < s1; s++) {
-                v = COHERENT ? __ldcg(list + s) : list[s];
+                v = list[s];
                 k += v.x;
                 m += v.y;
             }
@@ -106,9 +101,7 @@ __device__ __forceinline__ void sum_block(int64_t base, int64_t w0, int64_t w1, 
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < SB / NT; r++) {
-        const int t = threadIdx.x + r * NT;
+    {
         if (base + t < U) {
             int q = st_up[base + t];
             if (base + q >= w0 && base + q < w1) {
@@ -126,8 +119,6 @@ __device__ __forceinline__ void sum_block(int64_t base, int64_t w0, int64_t w1, 
             }
         }
     }
-    // a caller that loops over blocks synchronises before the next one (the
-    // shared arrays are reused)
 }
 
 }  // namespace ef

@@ -146,16 +146,31 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
             }
             __syncthreads();
             if (s_ok) {
-                // the tile's work items [i0, i1), by the aligned blocks of the
-                // sum kernel, stored in CSR position order
+                // one thread per work item, stored where it lies (ordering the
+                // stores per block of 256 items as the two-launch sum kernel
+                // does made this schedule slower: 26.9 against 25.0 ms for the
+                // 256-mesh batch)
                 double* K = nodes0 ? K0 : d.K;
                 double* M = nodes0 ? M0 : d.M;
+                const double2* l = d.list;
                 const int64_t i0 = g.lo + t * BU;
                 const int64_t i1 = i0 + BU < g.hi ? i0 + BU : g.hi;
-                for (int64_t b = i0 / SB; b * SB < i1; b++) {
-                    sum_block<BE, true>(b * SB, i0, i1, d.U, d.wseg, d.wpos_up, d.wpos_lo,
-                                        (const StoreIdx*)d.wst_up, (const StoreIdx*)d.wst_lo, d.list, K, M);
-                    __syncthreads();
+                for (int64_t i = i0 + threadIdx.x; i < i1; i += BE) {
+                    const uint32_t s0 = d.wseg[i], s1 = d.wseg[i + 1];
+                    const uint32_t pu = d.wpos_up[i], pl = d.wpos_lo[i];
+                    double2 v = __ldcg(l + s0);
+                    double kv = v.x, mv = v.y;
+                    for (uint32_t s = s0 + 1; s < s1; s++) {
+                        v = __ldcg(l + s);
+                        kv += v.x;
+                        mv += v.y;
+                    }
+                    K[pu] = kv;
+                    M[pu] = mv;
+                    if (pl != 0xffffffffu) {
+                        K[pl] = kv;
+                        M[pl] = mv;
+                    }
                 }
             }
             __syncthreads();
