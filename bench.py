@@ -596,39 +596,48 @@ def run_integration(args, dev, peaks):
     return out
 
 
-def run_majorant(args, dev, peaks):
+def run_majorant(args, dev, peaks, dim=2):
     """The library's share of the majorant minimisation (Sec. 4.1, Algorithm 1)
-    on the unit square with 2 m^2 triangles (m = 4096: Table 3's largest mesh,
-    33,554,432 triangles), 16-point rule (n = 4): RT0 K and M, the load
+    with the 16-point (2D) or 64-point (3D) rule (n = 4), on the unit square
+    with 2 m^2 triangles (m = 4096: Table 3's largest mesh, 33,554,432
+    triangles) or the unit cube with 6 c^3 Kuhn tetrahedra (c = 96: the size
+    of Table 4's largest mesh, 5,308,416 tetrahedra): RT0 K and M, the load
     vectors int grad v . phi (ef_load_vector) and int f div phi
     (ef_load_derivative), the error ||grad(u - v)||^2, and for each of the 3
-    iterations Table 3 prints ||grad v - y||^2 (ef_norm_l2) and ||div y + f||^2
-    (ef_norm_l2_derivative). The host solves are not part of it; grad v (per
-    element) and y are seeded normal values drawn on the device (they do not
-    change the work),
-    f and grad u are the bubble problem's. Rate = elements / time of all these
-    calls (one step)."""
+    iterations the tables print ||grad v - y||^2 (ef_norm_l2) and
+    ||div y + f||^2 (ef_norm_l2_derivative). The host solves are not part of
+    it; grad v (per element) and y are seeded normal values drawn on the
+    device (they do not change the work), f and grad u are the bubble
+    problem's. Rate = elements / time of all these calls (one step)."""
     import torch
 
     from paper_1409_4618_gb300 import edgefem as ef
 
-    m = args.majorant_m
-    nodes, elems = mg.kuhn_square(m)
+    if dim == 2:
+        m = args.majorant_m
+        nodes, elems = mg.kuhn_square(m)
+        name = f"rt2d_square{m}_majorant_q16"
+    else:
+        m = args.majorant_cube
+        nodes, elems = mg.kuhn_cube(m)
+        name = f"rt3d_kuhn{m}_majorant_q64"
     T, V = elems.shape[0], nodes.shape[0]
     tn = torch.from_numpy(nodes).to(dev)
-    plan = ef.Plan(1, 2, V, torch.from_numpy(elems).to(dev))
+    plan = ef.Plan(1, dim, V, torch.from_numpy(elems).to(dev))
     del elems
     n = 4
-    nq = n * n
-    x = plan.quad_points(tn, n)                                       # [nq, T, 2]
+    nq = n ** dim
+    x = plan.quad_points(tn, n)                                       # [nq, T, dim]
     a = x * (x - 1.0)
-    mf = (2.0 * (a[..., 0] + a[..., 1])).unsqueeze(-1).contiguous()   # -f = 2 (x(x-1) + y(y-1))
-    gu = torch.stack([(2.0 * x[..., 0] - 1.0) * a[..., 1], (2.0 * x[..., 1] - 1.0) * a[..., 0]], -1)
-    del x, a
+    # -f = 2 sum_i prod_{j != i} a_j;  (grad u)_i = (2 x_i - 1) prod_{j != i} a_j
+    others = [torch.prod(torch.cat([a[..., :c], a[..., c + 1:]], -1), -1) for c in range(dim)]
+    mf = (2.0 * sum(others)).unsqueeze(-1).contiguous()
+    gu = torch.stack([(2.0 * x[..., c] - 1.0) * others[c] for c in range(dim)], -1)
+    del x, a, others
     gen = torch.Generator(device=dev)
     gen.manual_seed(11)
-    gvt = torch.randn((T, 2), generator=gen, dtype=torch.float64, device=dev)
-    gv = gvt.unsqueeze(0).expand(nq, T, 2).contiguous()
+    gvt = torch.randn((T, dim), generator=gen, dtype=torch.float64, device=dev)
+    gv = gvt.unsqueeze(0).expand(nq, T, dim).contiguous()
     gerr = (gu - gv).contiguous()
     del gu, gvt
     f = (-mf).contiguous()
@@ -663,17 +672,19 @@ def run_majorant(args, dev, peaks):
     plan.check()
     ms = a0.elapsed_time(a1) / steps
     # algorithmic bytes of one step: per element the values at the points each
-    # call reads (8 B per component and point), connectivity (12 B) and the
-    # gathered coordinates (16 V / T) per call; the CSR values K, M (16 nnz);
-    # the local load entries written and re-read and the load vectors written;
-    # DOF ids, signs and the gathered y of the norms with y
+    # call reads (8 B per component and point), connectivity (4 (dim + 1) B)
+    # and the gathered coordinates (8 dim V / T) per call; the CSR values K, M
+    # (16 nnz); the local load entries written and re-read and the load vectors
+    # written; DOF ids, signs and the gathered y of the norms with y
+    nloc = dim + 1 if dim == 3 else 3
     calls = 4 + 2 * iters
-    per_pts = nq * 8 * (2 + 1 + 2 + iters * (2 + 1))
-    alg = (per_pts + calls * 12) * T + calls * 16 * V + 16 * plan.nnz + 2 * (2 * 3 * 8 * T + 8 * plan.n_dofs) \
-        + 2 * iters * (12 + 1 + 3 * 8) * T
+    per_pts = nq * 8 * (dim + 1 + dim + iters * (dim + 1))
+    alg = (per_pts + calls * 4 * (dim + 1)) * T + calls * 8 * dim * V + 16 * plan.nnz \
+        + 2 * (2 * nloc * 8 * T + 8 * plan.n_dofs) + 2 * iters * (4 * nloc + 1 + nloc * 8) * T
     gbs = alg / (ms / 1e3) / 1e9
-    out = {"value": T / (ms / 1e3) / 1e6, "unit": UNIT, "workload": f"rt2d_square{m}_majorant_q16",
-           "elements": int(T), "dofs": int(plan.n_dofs), "iterations": iters, "ms_per_step": ms,
+    out = {"value": T / (ms / 1e3) / 1e6, "unit": UNIT, "workload": name,
+           "elements": int(T), "dofs": int(plan.n_dofs), "iterations": iters, "points_per_element": nq,
+           "ms_per_step": ms,
            "calls_per_step": {"ef_assemble": 1, "ef_load_vector": 1, "ef_load_derivative": 1,
                               "ef_norm_l2": 1 + iters, "ef_norm_l2_derivative": iters},
            "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
@@ -809,7 +820,8 @@ def run_gpu(args):
         peaks, _ = _peaks()
         legs = {"batched": lambda: run_batched(args, dev, float("nan")), "adjoint": lambda: run_adjoint(args, dev),
                 "rt0": lambda: run_rt0(args, dev, peaks), "integration": lambda: run_integration(args, dev, peaks),
-                "majorant": lambda: run_majorant(args, dev, peaks), "lshape": lambda: run_lshape(args, dev, peaks)}
+                "majorant": lambda: run_majorant(args, dev, peaks), "lshape": lambda: run_lshape(args, dev, peaks),
+                "majorant3d": lambda: run_majorant(args, dev, peaks, dim=3)}
         print(json.dumps({"leg": args.only, **legs[args.only]()}), flush=True)
         return 0
     dist = None
@@ -985,6 +997,7 @@ def run_gpu(args):
         line["integration"] = run_integration(args, dev, peaks)
     if not args.no_majorant:
         line["majorant"] = run_majorant(args, dev, peaks)
+        line["majorant3d"] = run_majorant(args, dev, peaks, dim=3)
     if not args.no_lshape:
         line["lshape"] = run_lshape(args, dev, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -1008,7 +1021,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rt0", action="store_true")
-    ap.add_argument("--only", choices=["batched", "adjoint", "rt0", "integration", "majorant", "lshape"],
+    ap.add_argument("--only", choices=["batched", "adjoint", "rt0", "integration", "majorant", "majorant3d",
+                                       "lshape"],
                     help="run one of the other workloads by itself (profiling)")
     ap.add_argument("--adjoint-cube", type=int, default=96)
     ap.add_argument("--no-integration", action="store_true")
@@ -1017,6 +1031,8 @@ def main():
     ap.add_argument("--majorant-m", type=int, default=4096,
                     help="squares per axis of the majorant workload (2 m^2 triangles)")
     ap.add_argument("--majorant-steps", type=int, default=5)
+    ap.add_argument("--majorant-cube", type=int, default=96,
+                    help="cubes per axis of the 3D majorant workload (6 c^3 tetrahedra)")
     ap.add_argument("--no-lshape", action="store_true")
     ap.add_argument("--lshape-level", type=int, default=11,
                     help="level of the 2D L-shaped workload (6 4^L triangles)")
