@@ -4,7 +4,9 @@
 // block compact in space so that most nonzeros are completed inside it.
 //
 // Phase 1: thread t computes the signed local K and M of the block's t-th
-//   element (closed forms of ef_element.cuh) into shared memory, pair-major.
+//   element (closed forms of ef_element.cuh) and puts each value into shared
+//   memory at its place in the block's slot order (a plan-time map), so that
+//   the contributions of every slot lie contiguous there.
 // Phase 2: the CTA walks the block's "slots", the upper nonzeros its elements
 //   touch, each with the block's contributions to it listed in the order of
 //   the plan's global contribution list (ascending element id within a
@@ -232,8 +234,12 @@ __global__ void k_part_fix(const uint32_t* slot_off, int64_t nblocks, uint32_t* 
     if (b < nblocks && part_off[b] == NONE) part_off[b] = slot_off[b + 1];
 }
 
+// Per contribution i of the block-sorted list (block b, slot order): its
+// pair q and element r of the block give sidx[b][q][r] = i - b per_block, the
+// place where the element's thread puts that value in shared memory, so that
+// every slot's contributions lie contiguous and in list order there.
 __global__ void k_cidx(const uint64_t* keys, const uint32_t* bsorted, const uint32_t* perm, int64_t n, int64_t T,
-                       int BE, int64_t per_block, const uint32_t* rank, uint16_t* cidx, uint32_t* gpos,
+                       int BE, int64_t per_block, const uint32_t* rank, uint16_t* sidx, uint32_t* gpos,
                        unsigned long long* n_partial)
 {
     const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -246,16 +252,24 @@ __global__ void k_cidx(const uint64_t* keys, const uint32_t* bsorted, const uint
     const int64_t q = v / T, e = v % T;
     const int64_t b = i / per_block;
     const int64_t r = rank ? (int64_t)rank[e] : e;
-    cidx[i] = (uint16_t)(q * BE + (r - b * BE));
+    sidx[b * per_block + q * BE + (r - b * BE)] = (uint16_t)(i - b * per_block);
     gpos[i] = s;
 }
 
 // ---- assembly ---------------------------------------------------------------------
 
+// CTAs per SM that shared memory allows (local matrices of the block plus its
+// ticket queue): the register budget the compiler is held to
 template <int VAR, int BE>
-__global__ void __launch_bounds__(BE) k_fused(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
+constexpr int fused_min_blocks()
+{
+    return VAR == NED3 ? (BE == 128 ? 4 : 2) : (VAR == RT3 ? (BE == 128 ? 8 : 5) : (BE == 128 ? 8 : 4));
+}
+
+template <int VAR, int BE>
+__global__ void __launch_bounds__(BE, (fused_min_blocks<VAR, BE>())) k_fused(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
                                               const double* __restrict__ coeff, int64_t T,
-                                              const uint32_t* __restrict__ order, const uint16_t* __restrict__ cidx,
+                                              const uint32_t* __restrict__ order, const uint16_t* __restrict__ sidx,
                                               const uint32_t* __restrict__ gpos,
                                               const uint32_t* __restrict__ slot_off,
                                               const uint32_t* __restrict__ part_off,
@@ -276,33 +290,49 @@ __global__ void __launch_bounds__(BE) k_fused(const int32_t* __restrict__ elems,
     const int t = threadIdx.x;
     const int64_t b = blockIdx.x;
     if (t == 0) s_qn = 0;
+    // the block's slot ranges and this thread's first complete slot, loaded
+    // before the FP64 work so that they arrive while it runs
+    const uint32_t j0 = __ldg(slot_off + b), jp = __ldg(part_off + b), j1 = __ldg(slot_off + b + 1);
+    uint32_t j = j0 + t, info_n = 0, pa_n = 0, pb_n = 0;
+    if (j < jp) {
+        info_n = __ldg(sinfo + j);
+        pa_n = __ldg(posA + j);
+        pb_n = __ldg(posB + j);
+    }
     const int64_t i = b * BE + t;
     if (i < T) {
         const int64_t e = order ? (int64_t)__ldg(order + i) : i;
+        // where each of this element's contributions goes (slot order),
+        // loaded before the FP64 work (coalesced over the block's threads)
+        const uint16_t* si = sidx + b * (int64_t)(BE * E::NP) + t;
+        uint16_t pos[E::NP];
+#pragma unroll
+        for (int q = 0; q < E::NP; q++) pos[q] = __ldg(si + q * BE);
         double Kq[E::NP], Mq[E::NP];
         const double sigma = coeff ? __ldg(coeff + e) : 1.0;
         if (compute_element<VAR>(elems, nodes, sigma, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
 #pragma unroll
         for (int q = 0; q < E::NP; q++) {
-            smK[q * BE + t] = Kq[q];
-            smM[q * BE + t] = Mq[q];
+            smK[pos[q]] = Kq[q];
+            smM[pos[q]] = Mq[q];
         }
     }
     __syncthreads();
-    const uint16_t* c = cidx + b * (int64_t)(BE * E::NP);
     const uint32_t* g = gpos + b * (int64_t)(BE * E::NP);
-    const uint32_t j0 = __ldg(slot_off + b), jp = __ldg(part_off + b), j1 = __ldg(slot_off + b + 1);
-    // complete slots: sum in list order, store both triangles
-    for (uint32_t j = j0 + t; j < jp; j += BE) {
-        const uint32_t info = __ldg(sinfo + j);
-        const uint32_t pa = __ldg(posA + j), pb = __ldg(posB + j);
+    // complete slots: sum in list order, store both triangles; the next
+    // slot's metadata is loaded one iteration ahead
+    for (; j < jp; j += BE) {
+        const uint32_t info = info_n, pa = pa_n, pb = pb_n;
+        if (j + BE < jp) {
+            info_n = __ldg(sinfo + j + BE);
+            pa_n = __ldg(posA + j + BE);
+            pb_n = __ldg(posB + j + BE);
+        }
         const uint32_t start = info & 0xffffu, cnt = info >> 16;
-        uint32_t idx = c[start];
-        double k = smK[idx], m = smM[idx];
+        double k = smK[start], m = smM[start];
         for (uint32_t r = 1; r < cnt; r++) {
-            idx = c[start + r];
-            k += smK[idx];
-            m += smM[idx];
+            k += smK[start + r];
+            m += smM[start + r];
         }
         K[pa] = k;
         M[pa] = m;
@@ -316,9 +346,9 @@ __global__ void __launch_bounds__(BE) k_fused(const int32_t* __restrict__ elems,
         const uint32_t info = __ldg(sinfo + j);
         const uint32_t start = info & 0xffffu, cnt = info >> 16;
         for (uint32_t r = 0; r < cnt; r++) {
-            const uint32_t idx = c[start + r], s = __ldg(g + start + r);
-            partK[s] = smK[idx];
-            partM[s] = smM[idx];
+            const uint32_t s = __ldg(g + start + r);
+            partK[s] = smK[start + r];
+            partM[s] = smM[start + r];
         }
     }
     __threadfence();
@@ -525,7 +555,7 @@ int build_fused_block(ef_plan* p, int BE, const double* nodes, cudaStream_t s)
             !ok(cudaMalloc((void**)&p->d_fb_posB, (size_t)nslots * 4)) ||
             !ok(cudaMalloc((void**)&p->d_fb_slot_off, (size_t)(nblocks + 1) * 4)) ||
             !ok(cudaMalloc((void**)&p->d_fb_part_off, (size_t)nblocks * 4)) ||
-            !ok(cudaMalloc((void**)&p->d_fb_cidx, (size_t)n * 2)) ||
+            !ok(cudaMalloc((void**)&p->d_fb_cidx, (size_t)nblocks * per_block * 2)) ||   // [block][pair][element]
             !ok(cudaMalloc((void**)&p->d_fb_gpos, (size_t)n * 4))) {
             st = EF_ERR_OOM;
             break;
