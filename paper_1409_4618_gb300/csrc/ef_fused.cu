@@ -263,7 +263,7 @@ __global__ void k_cidx(const uint64_t* keys, const uint32_t* bsorted, const uint
 template <int VAR, int BE>
 constexpr int fused_min_blocks()
 {
-    return VAR == NED3 ? (BE == 128 ? 4 : 2) : (VAR == RT3 ? (BE == 128 ? 8 : 5) : (BE == 128 ? 8 : 4));
+    return VAR == NED3 ? (BE == 128 ? 4 : 2) : (VAR == RT3 ? (BE == 128 ? 8 : 5) : (BE == 128 ? 12 : 6));
 }
 
 template <int VAR, int BE>
