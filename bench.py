@@ -54,10 +54,13 @@ L2_BYTES = 129 * 1024 * 1024
 # leg has run (run_gpu runs it first), else the nominal figure above
 FP64_PEAK = {"T_ops_per_s": FP64_PEAK_TOPS, "source": "nominal"}
 # FP64 ops per tetrahedron of the adjoint kernel, counted from the source:
-# B 9, H 18, adj(H) 12, det 9, 1/|det| 8, r^3 2, a 6, a^T H a 9, Whitney
-# coefficients 17, P 30, <P, A> 6, J 6, A P 27, scale factors 14, Gamma 36,
-# B Gamma 27, node 0 6.
-ADJOINT_FP64_OPS_PER_TET = 9 + 18 + 12 + 9 + 8 + 2 + 6 + 9 + 17 + 30 + 6 + 6 + 27 + 14 + 36 + 27 + 6
+# B 9, H 18, adj(H) 12, det 9, 1/|det| 4 (two Newton steps), r^3 2, a 6,
+# a^T H a 9, Whitney coefficients 17, P 30, <P, A> 6, J 6, A P 27, scale
+# factors 14, Gamma 36, B Gamma 27, node 0 6.
+ADJOINT_FP64_OPS_PER_TET = 9 + 18 + 12 + 9 + 4 + 2 + 6 + 9 + 17 + 30 + 6 + 6 + 27 + 14 + 36 + 27 + 6
+# executed FP64 instructions per tetrahedron of the adjoint kernel (ncu sass
+# counters on the 24^3 cube: 43 DADD, 144 DFMA, 74 DMUL)
+ADJOINT_FP64_EXECUTED_PER_TET = 261
 # DRAM bytes (read + write) per element of the Nedelec-3D element kernel of
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
 # on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
@@ -167,10 +170,10 @@ class ClockSampler:
 # (kind, dim) -> DADD, DFMA, DMUL. Measured on the 24^3 cube (3D) and the
 # level-5 L-shape (2D); the counts do not depend on the mesh.
 ELEMENT_KERNEL_FP64_EXECUTED = {
-    (2, 3): {"dadd": 54, "dfma": 46, "dmul": 32},
-    (1, 3): {"dadd": 21, "dfma": 37, "dmul": 17},
-    (1, 2): {"dadd": 10, "dfma": 18, "dmul": 10},
-    (2, 2): {"dadd": 18, "dfma": 18, "dmul": 9},
+    (2, 3): {"dadd": 53, "dfma": 45, "dmul": 32},
+    (1, 3): {"dadd": 20, "dfma": 36, "dmul": 17},
+    (1, 2): {"dadd": 9, "dfma": 17, "dmul": 10},
+    (2, 2): {"dadd": 17, "dfma": 17, "dmul": 9},
 }
 ELEMENT_KERNEL_FP64_MIX = ELEMENT_KERNEL_FP64_EXECUTED[(2, 3)]
 
@@ -212,18 +215,18 @@ def run_fp64_probe(gpu_index: int) -> dict:
 def fp64_ops_per_element(kind: int, dim: int) -> int:
     """FP64 pipe operations (DADD, DMUL, DFMA each 1) of one element's local
     matrices in the closed forms of csrc/ef_element.cuh, counted from the
-    source; the library reciprocal 1/|det| is counted as 8."""
+    source; the reciprocal 1/|det| is two Newton steps, 4 DFMA."""
     if (kind, dim) == (2, 3):
-        # B 9, H 18, adj(H) 12, det 9, 1/|det| 8, sigma*r 1, K: 1 + 6 + 15, M: 1 + 6 + 41
-        return 9 + 18 + 12 + 9 + 8 + 1 + 22 + 48
+        # B 9, H 18, adj(H) 12, det 9, 1/|det| 4, sigma*r 2, K: 1 + 6 + 15, M: 1 + 6 + 41
+        return 9 + 18 + 12 + 9 + 4 + 2 + 22 + 48
     if (kind, dim) == (1, 3):
-        # B 9, H 18, det 9, 1/|det| 8, sigma*r 1, row sums 6, c0 5, scales 5, q 3, t 3, entries 12, K 1
-        return 9 + 18 + 9 + 8 + 1 + 6 + 5 + 5 + 3 + 3 + 12 + 1
+        # B 9, H 18, det 9, 1/|det| 4, sigma*r 2, row sums 6, c0 5, scales 4, q 3, t 3, entries 12, K 1
+        return 9 + 18 + 9 + 4 + 2 + 6 + 5 + 4 + 3 + 3 + 12 + 1
     if (kind, dim) == (1, 2):
-        # B 4, H 6, det 2, 1/|det| 8, sigma*r 2, cM 1, row sums 2, c0 3, scales 2, c0s q 3, t 2, entries 6, K 1
-        return 4 + 6 + 2 + 8 + 2 + 1 + 2 + 3 + 2 + 3 + 2 + 6 + 1
-    # 2D Nedelec: B 4, H 6, det 2, 1/|det| 8, sigma*r 2, cM 1, g 3, g01 g02 2, g00 1, entries 18, K 1
-    return 4 + 6 + 2 + 8 + 2 + 1 + 3 + 2 + 1 + 18 + 1
+        # B 4, H 6, det 2, 1/|det| 4, sigma*r 2, cM 1, row sums 2, c0 3, scales 2, c0s q 3, t 2, entries 6, K 1
+        return 4 + 6 + 2 + 4 + 2 + 1 + 2 + 3 + 2 + 3 + 2 + 6 + 1
+    # 2D Nedelec: B 4, H 6, det 2, 1/|det| 4, sigma*r 2, cM 1, g 3, g01 g02 2, g00 1, entries 18, K 1
+    return 4 + 6 + 2 + 4 + 2 + 1 + 3 + 2 + 1 + 18 + 1
 
 
 def run_reference(args):
@@ -742,6 +745,9 @@ def run_adjoint(args, dev):
                     "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-ops/s",
                     "frac": ops / (ms_adj / 1e3) / 1e12 / FP64_PEAK["T_ops_per_s"],
                     "peak_source": FP64_PEAK["source"],
+                    "executed_per_elem": ADJOINT_FP64_EXECUTED_PER_TET,
+                    "frac_executed": ADJOINT_FP64_EXECUTED_PER_TET * T / (ms_adj / 1e3) / 1e12
+                    / FP64_PEAK["T_ops_per_s"],
                     "note": "whole ef_adjoint call (element kernel ~92 % of it)"}}
     plan.close()
     return out

@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(ADJ_TPB, 3) k_adjoint_ned3(const int32_t* __re
         const double cx = fma(B[1][1], B[2][2], -(B[2][1] * B[1][2]));
         const double cy = fma(B[2][1], B[0][2], -(B[0][1] * B[2][2]));
         const double cz = fma(B[0][1], B[1][2], -(B[1][1] * B[0][2]));
-        const double adet = fabs(fma(B[2][0], cz, fma(B[1][0], cy, B[0][0] * cx)));
+        const double adet = abs_bits(fma(B[2][0], cz, fma(B[1][0], cy, B[0][0] * cx)));
         if (not_positive(adet)) atomicOr(status, ST_DEGENERATE);
-        const double r = 1.0 / adet;
+        const double r = recip_positive(adet);
         const double r3 = r * r * r;
 
         // K part: aHa = a^T H a over the symmetric H

@@ -26,7 +26,7 @@
 // Signs are applied by flipping the IEEE sign bit (integer XOR), so they cost
 // no floating-point work. |det B| enters only through r = 1/|det B|, with det B
 // from the triple product (accurate to cond(B) eps, also on nearly flat
-// elements).
+// elements) and r by Newton-Raphson steps (recip_positive).
 #pragma once
 
 #include <stdint.h>
@@ -38,9 +38,18 @@ __device__ __constant__ const int8_t kEdge2[3][2] = {{1, 2}, {2, 0}, {0, 1}};
 __device__ __constant__ const int8_t kEdge3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {2, 3}, {3, 1}};
 __device__ __constant__ const int8_t kFace3[4][4] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 3, 1}, {1, 2, 3, 0}};
 
+// Sign flips and absolute values as 32-bit integer operations on the high
+// word: written on the 64-bit pattern, the compiler turned some of them into
+// FP64 additions (measured: 9 FP64 instructions per 3D Nedelec element), and
+// the FP64 pipe bounds the element kernels.
 __device__ __forceinline__ double flip_if(double x, uint32_t f)
 {
-    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(f & 1u) << 63));
+    return __hiloint2double(__double2hiint(x) ^ (int)((f & 1u) << 31), __double2loint(x));
+}
+
+__device__ __forceinline__ double abs_bits(double x)
+{
+    return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
 }
 
 // Orientation sign bits (bit k set iff s_k = -1), from global node ids only.
@@ -85,11 +94,27 @@ __device__ __forceinline__ double twice(double x)
     return x + x;
 }
 
-// det H <= 0 (or NaN) marks a degenerate element; tested on the bit pattern.
+// |det B| that is not a positive normal number (zero, below 2^-1022, or not
+// finite) marks a degenerate element; tested on the bit pattern.
 __device__ __forceinline__ bool not_positive(double x)
 {
     long long b = __double_as_longlong(x);
-    return b <= 0 || (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+    return b < 0x0010000000000000ll || (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+}
+
+// 1/x for a positive normal x by Newton-Raphson iteration for the reciprocal,
+// y <- y + y (1 - x y) (quadratic convergence: a relative error e becomes e^2
+// plus one rounding), started from the hardware's approximate reciprocal (PTX
+// rcp.approx.ftz.f64, relative error below 2^-22): two steps reach double
+// precision to about one ulp. Four DFMA on the FP64 pipe, which bounds the
+// element kernels, against the longer sequence of the IEEE division. Callers
+// flag x outside the positive normals as degenerate (not_positive).
+__device__ __forceinline__ double recip_positive(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
 }
 
 // ---- 3D Nedelec: 21 + 21 upper entries ---------------------------------------
@@ -115,9 +140,9 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     // det B by the triple product e1 . (e2 x e3): its error grows like cond(B),
     // where det(H) = det(B)^2 from the Gram matrix would grow like cond(B)^2
     const double cx = fma(e2y, e3z, -(e2z * e3y)), cy = fma(e2z, e3x, -(e2x * e3z)), cz = fma(e2x, e3y, -(e2y * e3x));
-    const double adet = fabs(fma(e1z, cz, fma(e1y, cy, e1x * cx)));
+    const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, e1x * cx)));
     const bool bad = not_positive(adet);
-    const double r = 1.0 / adet;
+    const double r = recip_positive(adet);
     const double srK = sigmaK * r, srM = sigmaM * r;
 
     // K_kl = (2 sigma / (3|det|)) w_k . w_l
@@ -204,9 +229,9 @@ __device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigmaK
     const double H13 = fma(e1z, e3z, fma(e1y, e3y, e1x * e3x));
     const double H23 = fma(e2z, e3z, fma(e2y, e3y, e2x * e3x));
     const double cx = fma(e2y, e3z, -(e2z * e3y)), cy = fma(e2z, e3x, -(e2x * e3z)), cz = fma(e2x, e3y, -(e2y * e3x));
-    const double det = fma(e1z, cz, fma(e1y, cy, e1x * cx));
-    const bool bad = not_positive(fabs(det));
-    const double r = 1.0 / fabs(det);
+    const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, e1x * cx)));
+    const bool bad = not_positive(adet);
+    const double r = recip_positive(adet);
     const double srK = sigmaK * r, srM = sigmaM * r;
     // M: sigma/(120|det|) [c0 - 5 (S.y_a + S.y_b) + 20 y_a.y_b]
     const double r1 = H11 + H12 + H13, r2 = H12 + H22 + H23, r3 = H13 + H23 + H33;
@@ -249,9 +274,9 @@ __device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigmaK
     const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1];
     const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1];
     const double H11 = fma(e1y, e1y, e1x * e1x), H22 = fma(e2y, e2y, e2x * e2x), H12 = fma(e1y, e2y, e1x * e2x);
-    const double det = fma(e1x, e2y, -(e1y * e2x));
-    const bool bad = not_positive(fabs(det));
-    const double r = 1.0 / fabs(det);
+    const double adet = abs_bits(fma(e1x, e2y, -(e1y * e2x)));
+    const bool bad = not_positive(adet);
+    const double r = recip_positive(adet);
     const double srK = sigmaK * r, srM = sigmaM * r;
     const double cM = srM * (1.0 / 24.0);
     if (VAR == 0) {

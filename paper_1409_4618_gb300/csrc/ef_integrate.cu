@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2(const int32_t* __restrict__ el
                 s = fma(table[q][3], d2, s);
             }
         }
-        acc = fabs(det) * s;
+        acc = abs_bits(det) * s;
         if (elem_out) elem_out[e] = acc;
     }
     red[threadIdx.x] = acc;
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(ITPB) k_load_local(const int32_t* __restrict__
         }
     }
     const uint32_t neg = __ldg(signbits + e);
-    const double adet = fabs(det);
+    const double adet = abs_bits(det);
 #pragma unroll
     for (int k = 0; k < NL; k++) {
         const double v = adet * l[k];
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2_deriv(const int32_t* __restric
             }
             s = fma(table[q][3], d2, s);
         }
-        acc = fabs(det) * s;
+        acc = abs_bits(det) * s;
         if (elem_out) elem_out[e] = acc;
     }
     red[threadIdx.x] = acc;
