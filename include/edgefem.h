@@ -58,7 +58,7 @@ extern "C" {
 #define EF_OK 0
 #define EF_ERR_ARG (-1)          /* bad pointer, size, kind or dim; repeated node in an element */
 #define EF_ERR_RANGE (-2)        /* node id outside [0, n_nodes) */
-#define EF_ERR_DEGENERATE (-3)   /* an element has det B_K = 0 */
+#define EF_ERR_DEGENERATE (-3)   /* an element has det B_K = 0 (|det B_K| below 2^-1022, or not finite) */
 #define EF_ERR_KEY_OVERFLOW (-4) /* 3D RT0 face keys need n_nodes^3 < 2^64 (n_nodes <= 2642245) */
 #define EF_ERR_OOM (-5)          /* device allocation failed */
 #define EF_ERR_CUDA (-6)         /* a CUDA runtime call failed (see ef_last_error) */
