@@ -65,7 +65,7 @@ ADJOINT_FP64_EXECUTED_PER_TET = 261
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
 # on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
 # to the elements.
-ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (76.359936e6 + 166.353920e6) / 663552
+ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (75.725056e6 + 166.208000e6) / 663552
 
 
 def _peaks():
