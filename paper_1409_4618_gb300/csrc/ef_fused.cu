@@ -238,7 +238,7 @@ __global__ void k_part_fix(const uint32_t* slot_off, int64_t nblocks, uint32_t* 
 // pair q and element r of the block give sidx[b][q][r] = i - b per_block, the
 // place where the element's thread puts that value in shared memory, so that
 // every slot's contributions lie contiguous and in list order there.
-__global__ void k_cidx(const uint64_t* keys, const uint32_t* bsorted, const uint32_t* perm, int64_t n, int64_t T,
+__global__ void k_slot_places(const uint64_t* keys, const uint32_t* bsorted, const uint32_t* perm, int64_t n, int64_t T,
                        int BE, int64_t per_block, const uint32_t* rank, uint16_t* sidx, uint32_t* gpos,
                        unsigned long long* n_partial)
 {
@@ -400,7 +400,7 @@ int launch_fused_t(const ef_plan* p, const double* nodes, const double* coeff, d
     double* partK = p->d_local;
     double* partM = p->d_local + (int64_t)p->np * p->T;
     k_fused<VAR, BE><<<(unsigned)p->fb_nblocks, BE, smem, s>>>(
-        p->d_elems, nodes, coeff, p->T, p->d_fb_order, p->d_fb_cidx, p->d_fb_gpos, p->d_fb_slot_off,
+        p->d_elems, nodes, coeff, p->T, p->d_fb_order, p->d_fb_sidx, p->d_fb_gpos, p->d_fb_slot_off,
         p->d_fb_part_off, p->d_fb_sinfo, p->d_fb_posA, p->d_fb_posB, p->d_seg, p->d_pos_up, p->d_pos_lo, p->d_px_uid,
         p->d_px_nb, p->d_px_cnt, K, M, partK, partM, p->d_status);
     EF_CUDA(cudaGetLastError());
@@ -425,14 +425,14 @@ size_t smem_needed(const ef_plan* p, int BE)
 
 void free_fused(ef_plan* p)
 {
-    void* ptrs[] = {p->d_fb_slot_off, p->d_fb_part_off, p->d_fb_sinfo, p->d_fb_cidx, p->d_fb_gpos,
+    void* ptrs[] = {p->d_fb_slot_off, p->d_fb_part_off, p->d_fb_sinfo, p->d_fb_sidx, p->d_fb_gpos,
                     p->d_fb_posA,     p->d_fb_posB,     p->d_px_uid,   p->d_px_nb,   p->d_px_cnt,
                     p->d_fb_order};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     p->d_fb_slot_off = p->d_fb_part_off = p->d_fb_sinfo = p->d_fb_posA = p->d_fb_posB = nullptr;
     p->d_px_uid = p->d_px_nb = p->d_px_cnt = p->d_fb_gpos = p->d_fb_order = nullptr;
-    p->d_fb_cidx = nullptr;
+    p->d_fb_sidx = nullptr;
     p->fb_block = 0;
     p->fb_nblocks = 0;
     p->fb_nslots = 0;
@@ -555,7 +555,7 @@ int build_fused_block(ef_plan* p, int BE, const double* nodes, cudaStream_t s)
             !ok(cudaMalloc((void**)&p->d_fb_posB, (size_t)nslots * 4)) ||
             !ok(cudaMalloc((void**)&p->d_fb_slot_off, (size_t)(nblocks + 1) * 4)) ||
             !ok(cudaMalloc((void**)&p->d_fb_part_off, (size_t)nblocks * 4)) ||
-            !ok(cudaMalloc((void**)&p->d_fb_cidx, (size_t)nblocks * per_block * 2)) ||   // [block][pair][element]
+            !ok(cudaMalloc((void**)&p->d_fb_sidx, (size_t)nblocks * per_block * 2)) ||   // [block][pair][element]
             !ok(cudaMalloc((void**)&p->d_fb_gpos, (size_t)n * 4))) {
             st = EF_ERR_OOM;
             break;
@@ -587,7 +587,7 @@ int build_fused_block(ef_plan* p, int BE, const double* nodes, cudaStream_t s)
         }
         k_part_fix<<<grid_for(nblocks), TPB, 0, s>>>(p->d_fb_slot_off, nblocks, p->d_fb_part_off);
         cudaMemsetAsync(npart, 0, 8, s);
-        k_cidx<<<grid_for(n), TPB, 0, s>>>(keys, bsorted, p->d_perm, n, T, BE, per_block, rank, p->d_fb_cidx,
+        k_slot_places<<<grid_for(n), TPB, 0, s>>>(keys, bsorted, p->d_perm, n, T, BE, per_block, rank, p->d_fb_sidx,
                                            p->d_fb_gpos, npart);
         // the largest number of partial slots of a block bounds its ticket queue
         std::vector<uint32_t> so((size_t)nblocks + 1), po((size_t)nblocks);

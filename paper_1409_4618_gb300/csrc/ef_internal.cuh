@@ -120,7 +120,7 @@ struct ef_plan {
     uint32_t* d_fb_sinfo;     // per slot: start | count << 16
     uint32_t* d_fb_posA;      // per slot: CSR position of (r,c), or the split index if partial
     uint32_t* d_fb_posB;      // per slot: CSR position of (c,r), or 0xffffffff
-    uint16_t* d_fb_cidx;      // per block [pair][element in block]: the value's place in the block's slot order
+    uint16_t* d_fb_sidx;      // per block [pair][element in block]: the value's place in the block's slot order
     uint32_t* d_fb_gpos;      // per contribution, block-major: its position in the global list
     uint32_t* d_px_uid;       // upper nonzeros split across blocks
     uint32_t* d_px_nb;        // per split nonzero: blocks contributing to it
