@@ -11,12 +11,15 @@ shape-optimisation loop where only coordinates and coefficients change.
 Prints one JSON line: throughput (M elements / s), e2e through the host-buffer
 C-ABI call, the roofline of the step's dominant kernel (timed per launch by
 CUDA events the library records on the launching stream inside the timed
-region), the HBM fraction of the whole step, the clocks seen while timing,
-the CPU oracle timed on this host, and the other workloads: batched (256
-meshes), adjoint (96^3), RT0 (3D 128^3, 2D 32^2) and the vectorised
+region) against this GPU's FP64 pipe rate measured first by the library's
+probe (ef_fp64_probe), the HBM fraction of the whole step, the clocks seen
+while timing, the CPU oracle timed on this host, and the other workloads:
+batched (256 meshes, one ef_batch_assemble call per step replayed from a
+CUDA graph), adjoint (96^3), RT0 (3D 128^3, 2D 32^2) and the vectorised
 integration (L2 error at 27 points per element), the library share of the
-majorant minimisation (Sec. 4.1) on the 33.5 M-triangle square, and the 2D
-RT0 and Nedelec assembly on Table 1's L-shaped domain (level 11).
+majorant minimisation (Sec. 4.1) on the 33.5 M-triangle square and on the
+5.3 M-tetrahedron cube, and the 2D RT0 and Nedelec assembly on Table 1's
+L-shaped domain (level 11).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
