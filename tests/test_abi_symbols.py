@@ -59,6 +59,15 @@ def test_argument_errors_need_no_gpu():
     assert lib.ef_plan_create(2, 3, 1 << 31, 1, ctypes.c_void_p(16), None, ctypes.byref(h)) == ef.EF_ERR_SIZE
     assert lib.ef_plan_create(2, 3, 100, 1 << 28, ctypes.c_void_p(16), None, ctypes.byref(h)) == ef.EF_ERR_SIZE
     assert lib.ef_assemble(None, None, None, None, None, None) == ef.EF_ERR_ARG
+    assert lib.ef_assemble_noalloc(None, None, None, None, None, None) == ef.EF_ERR_ARG
+    assert lib.ef_plan_set_fused(None, None, 128, None) == ef.EF_ERR_ARG
+    assert lib.ef_batch_assemble(None, None, None, None, None, None) == ef.EF_ERR_ARG
+    assert lib.ef_batch_plan_create(1, 3, 0, None, None, None, None, ctypes.byref(h)) == ef.EF_ERR_ARG
+    assert lib.ef_batch_plan_create(3, 3, 1, None, None, None, None, ctypes.byref(h)) == ef.EF_ERR_ARG
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    assert lib.ef_fp64_probe(3, 10, ctypes.c_void_p(16), ctypes.byref(rate), ctypes.byref(ms), None) == ef.EF_ERR_ARG
+    assert lib.ef_fp64_probe(0, 0, ctypes.c_void_p(16), ctypes.byref(rate), ctypes.byref(ms), None) == ef.EF_ERR_ARG
+    assert lib.ef_fp64_probe(0, 10, None, ctypes.byref(rate), ctypes.byref(ms), None) == ef.EF_ERR_ARG
     assert h.value is None
 
 
@@ -85,6 +94,29 @@ def test_binding_rejects_wrong_sizes_before_the_library():
                  lambda: plan.norm_l2_derivative(ok, torch.zeros((8, 48, 3), dtype=torch.float64), 2,
                                                  torch.zeros(99, dtype=torch.float64)),
                  lambda: plan.adjoint(ok, None, torch.zeros(98, dtype=torch.float64),
-                                      torch.zeros(97, dtype=torch.float64))):
+                                      torch.zeros(97, dtype=torch.float64)),
+                 lambda: plan.assemble_noalloc(ok, None, torch.zeros(999, dtype=torch.float64)),
+                 lambda: plan.set_fused(torch.zeros(80, dtype=torch.float64), 128)):
         with pytest.raises(ValueError, match="entries|shape"):   # not the closed-handle error
             call()
+
+
+def test_batch_binding_rejects_wrong_sizes_before_the_library():
+    """The batch calls take host tables of device pointers; the binding checks
+    the number of meshes and each buffer's size first (no GPU needed)."""
+    import torch
+
+    from paper_1409_4618_gb300 import edgefem as ef
+
+    b = ef.Batch.__new__(ef.Batch)
+    b.kind, b.dim, b.n = ef.EF_NED1, 3, 2
+    b.n_nodes, b.n_elems, b.nnz, b.n_dofs = [27, 8], [48, 6], [1000, 100], [98, 19]
+    b._h = None
+    nodes = [torch.zeros(81, dtype=torch.float64), torch.zeros(24, dtype=torch.float64)]
+    K = [torch.zeros(1000, dtype=torch.float64), torch.zeros(100, dtype=torch.float64)]
+    with pytest.raises(ValueError, match="meshes"):
+        b.tables(nodes[:1], None, K, K)
+    with pytest.raises(ValueError, match="entries"):
+        b.tables(nodes, None, [K[0], torch.zeros(99, dtype=torch.float64)], K)
+    with pytest.raises(ValueError, match="entries"):
+        b.tables(nodes, [torch.zeros(48, dtype=torch.float64), torch.zeros(5, dtype=torch.float64)], K, K)
