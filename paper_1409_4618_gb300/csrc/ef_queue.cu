@@ -51,7 +51,7 @@ __device__ __forceinline__ uint64_t global_ns()
 
 // CTAs per SM the kernel is compiled for: 80 registers per thread, enough for
 // the 3D Nedelec element matrices without spills.
-constexpr int queue_min_blocks(int BE) { return BE == 128 ? 6 : 3; }
+constexpr int queue_min_blocks(int BE) { return BE == 128 ? 8 : 4; }
 
 __device__ __forceinline__ int find_segment(const QueueSegment* __restrict__ seg, int nseg, int64_t k)
 {
