@@ -49,8 +49,11 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// CTAs per SM the kernel is compiled for: 80 registers per thread, enough for
-// the 3D Nedelec element matrices without spills.
+// CTAs per SM the kernel is compiled for: 64 registers per thread (8 CTAs
+// of 128 threads), so that the memory-bound sum tiles have 32 warps per SM;
+// the 3D Nedelec element matrices then spill about 100 bytes per thread.
+// Measured on the 256-mesh batch: 24.4 ms against 24.8 ms with 80 registers
+// (6 CTAs, no spills).
 constexpr int queue_min_blocks(int BE) { return BE == 128 ? 8 : 4; }
 
 __device__ __forceinline__ int find_segment(const QueueSegment* __restrict__ seg, int nseg, int64_t k)
