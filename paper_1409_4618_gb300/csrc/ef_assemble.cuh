@@ -30,35 +30,97 @@ __device__ __forceinline__ void load_ids(const int32_t* __restrict__ elems, int6
     }
 }
 
-// Signed local K, M upper triangles of element e, K times sigmaK and M times
-// sigmaM; true if degenerate.
 template <int VAR>
-__device__ __forceinline__ bool compute_element(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
-                                                double sigmaK, double sigmaM, int64_t e,
-                                                double (&Kq)[ElemTraits<VAR>::NP], double (&Mq)[ElemTraits<VAR>::NP])
+__device__ __forceinline__ void load_coords(const double* __restrict__ nodes, const int32_t (&g)[ElemTraits<VAR>::NV],
+                                            double (&p)[ElemTraits<VAR>::NV][ElemTraits<VAR>::DIM])
 {
     using E = ElemTraits<VAR>;
-    int32_t g[E::NV];
+#pragma unroll
+    for (int a = 0; a < E::NV; a++)
+#pragma unroll
+        for (int c = 0; c < E::DIM; c++) p[a][c] = __ldg(nodes + (int64_t)g[a] * E::DIM + c);
+}
+
+template <int VAR>
+__device__ __forceinline__ void load_element(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
+                                             const double* __restrict__ coeffK, const double* __restrict__ coeffM,
+                                             int64_t e, int32_t (&g)[ElemTraits<VAR>::NV],
+                                             double (&p)[ElemTraits<VAR>::NV][ElemTraits<VAR>::DIM], double& sigmaK,
+                                             double& sigmaM)
+{
     load_ids<VAR>(elems, e, g);
-    const uint32_t neg = sign_bits<VAR>(g);
-    if constexpr (E::DIM == 3) {
-        double p[4][3];
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) p[a][c] = __ldg(nodes + (int64_t)g[a] * 3 + c);
-        if constexpr (VAR == NED3)
-            return ned3_local(p, sigmaK, sigmaM, neg, Kq, Mq);
-        else
-            return rt3_local(p, sigmaK, sigmaM, neg, Kq, Mq);
-    } else {
-        double p[3][2];
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int c = 0; c < 2; c++) p[a][c] = __ldg(nodes + (int64_t)g[a] * 2 + c);
-        return tri_local<VAR == NED2 ? 2 : 0>(p, sigmaK, sigmaM, neg, Kq, Mq);
+    load_coords<VAR>(nodes, g, p);
+    sigmaK = coeffK ? __ldg(coeffK + e) : 1.0;
+    sigmaM = coeffM == coeffK ? sigmaK : (coeffM ? __ldg(coeffM + e) : 1.0);
+}
+
+// Numbers carried from an element routine's first part (all its products) to
+// its second (additions and FMAs).
+template <int VAR>
+struct ScaledTraits {
+    static constexpr int N = (VAR == NED3 || VAR == RT3) ? 12 : TriScaled<VAR == NED2 ? 2 : 0>::N;
+};
+
+template <int VAR, class MUL>
+__device__ __forceinline__ bool element_scaled(MUL& mul,
+                                               const double (&p)[ElemTraits<VAR>::NV][ElemTraits<VAR>::DIM],
+                                               double sigmaK, double sigmaM, double (&s)[ScaledTraits<VAR>::N])
+{
+    if constexpr (VAR == NED3)
+        return ned3_scaled(mul, p, sigmaK, sigmaM, s);
+    else if constexpr (VAR == RT3)
+        return rt3_scaled(mul, p, sigmaK, sigmaM, s);
+    else
+        return tri_scaled<VAR == NED2 ? 2 : 0>(mul, p, sigmaK, sigmaM, s);
+}
+
+// Signed local K, M upper triangles of element e, K times its coefficient in
+// coeffK and M times its coefficient in coeffM (NULL: 1); true if degenerate.
+// With INT_MUL the products run on the integer pipes (IntMul). An element in
+// which an operand or a product leaves the normal numbers and zero
+// (subnormal, infinite, NaN, overflowing: IntMul sets off) is repeated with
+// the FP64 multiply from its data loaded again (so that none of it has to
+// stay in registers meanwhile). Either way the entries are those of the
+// routine with FP64 products, bit for bit, so a kernel may take whichever
+// form runs faster in it (the integer form needs more registers).
+template <int VAR, bool INT_MUL = true>
+__device__ __forceinline__ bool compute_element(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
+                                                const double* __restrict__ coeffK, const double* __restrict__ coeffM,
+                                                int64_t e, double (&Kq)[ElemTraits<VAR>::NP],
+                                                double (&Mq)[ElemTraits<VAR>::NP])
+{
+    using E = ElemTraits<VAR>;
+    double s[ScaledTraits<VAR>::N];
+    uint32_t neg;
+    bool bad;
+    {
+        int32_t g[E::NV];
+        double p[E::NV][E::DIM], sigmaK, sigmaM;
+        load_element<VAR>(elems, nodes, coeffK, coeffM, e, g, p, sigmaK, sigmaM);
+        neg = sign_bits<VAR>(g);
+        if constexpr (!INT_MUL) {
+            FpMul fm;
+            bad = element_scaled<VAR>(fm, p, sigmaK, sigmaM, s);
+        } else {
+            IntMul im;
+            bad = element_scaled<VAR>(im, p, sigmaK, sigmaM, s);
+            if (im.off) {
+                // the index through an opaque move: the loads are not merged with the ones above
+                int64_t e2 = e;
+                asm volatile("" : "+l"(e2));
+                load_element<VAR>(elems, nodes, coeffK, coeffM, e2, g, p, sigmaK, sigmaM);
+                FpMul fm;
+                bad = element_scaled<VAR>(fm, p, sigmaK, sigmaM, s);
+            }
+        }
     }
+    if constexpr (VAR == NED3)
+        ned3_entries(s, neg, Kq, Mq);
+    else if constexpr (VAR == RT3)
+        rt3_entries(s, neg, Kq, Mq);
+    else
+        tri_entries<VAR == NED2 ? 2 : 0>(s, neg, Kq, Mq);
+    return bad;
 }
 
 // ---- the fixed-order sum of one aligned block of work items ------------------

@@ -31,6 +31,8 @@
 
 #include <stdint.h>
 
+#include "ef_intmul.cuh"
+
 namespace ef {
 
 // local DOF entities (Fig. 1), 0-based
@@ -83,22 +85,32 @@ __device__ __forceinline__ uint32_t sign_bits(const int32_t* g)
     return bits;
 }
 
-// 2x exactly: for normal x whose double stays finite, add one to the
-// exponent field on the integer pipe; otherwise (zero, subnormal, overflow,
-// inf, NaN) fall back to x + x.
+// 2x exactly, as x + x gives it, on the integer pipe only: for normal x whose
+// double stays finite, add one to the exponent field; zero and subnormal x
+// shift their magnitude left (a carry into the exponent field is exact);
+// 2x above the largest double is infinity; infinity stays, NaN is made quiet.
 __device__ __forceinline__ double twice(double x)
 {
-    const long long b = __double_as_longlong(x);
-    const unsigned ex = (unsigned)(b >> 52) & 0x7ffu;
-    if (ex - 1u < 0x7fdu) return __longlong_as_double(b + (1ll << 52));
-    return x + x;
+    const uint64_t b = bits_of(x);
+    const uint64_t s = b & 0x8000000000000000ull, m = b & 0x7fffffffffffffffull;
+    const unsigned ex = (unsigned)(m >> 52);
+    uint64_t r;
+    if (ex - 1u < 0x7fdu)
+        r = b + (1ull << 52);
+    else if (ex == 0u)
+        r = s | (m << 1);
+    else if (ex == 0x7feu)
+        r = s | 0x7ff0000000000000ull;
+    else
+        r = b | (m > 0x7ff0000000000000ull ? 0x0008000000000000ull : 0ull);
+    return double_of(r);
 }
 
 // |det B| that is not a positive normal number (zero, below 2^-1022, or not
 // finite) marks a degenerate element; tested on the bit pattern.
 __device__ __forceinline__ bool not_positive(double x)
 {
-    long long b = __double_as_longlong(x);
+    const long long b = (long long)bits_of(x);
     return b < 0x0010000000000000ll || (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
 }
 
@@ -118,36 +130,53 @@ __device__ __forceinline__ double recip_positive(double x)
 }
 
 // ---- 3D Nedelec: 21 + 21 upper entries ---------------------------------------
-__device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigmaK, double sigmaM, uint32_t neg,
-                                           double (&Kq)[21], double (&Mq)[21])
+// Every product of the routine is in its first part, which reduces the element
+// to twelve numbers: s[0..5] = h = (2 sigma_K / (3|det|)) H and s[6..11] = g =
+// (sigma_M / (120|det|)) adj(H) (upper triangles, order 11, 22, 33, 12, 13, 23).
+// MUL forms the products (IntMul on the integer pipes, or FpMul); true if
+// degenerate.
+template <class MUL>
+__device__ __forceinline__ bool ned3_scaled(MUL& mul, const double (&p)[4][3], double sigmaK, double sigmaM,
+                                            double (&s)[12])
 {
     const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
     const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
     const double e3x = p[3][0] - p[0][0], e3y = p[3][1] - p[0][1], e3z = p[3][2] - p[0][2];
-    const double H11 = fma(e1z, e1z, fma(e1y, e1y, e1x * e1x));
-    const double H22 = fma(e2z, e2z, fma(e2y, e2y, e2x * e2x));
-    const double H33 = fma(e3z, e3z, fma(e3y, e3y, e3x * e3x));
-    const double H12 = fma(e1z, e2z, fma(e1y, e2y, e1x * e2x));
-    const double H13 = fma(e1z, e3z, fma(e1y, e3y, e1x * e3x));
-    const double H23 = fma(e2z, e3z, fma(e2y, e3y, e2x * e3x));
+    const double H11 = fma(e1z, e1z, fma(e1y, e1y, mul(e1x, e1x)));
+    const double H22 = fma(e2z, e2z, fma(e2y, e2y, mul(e2x, e2x)));
+    const double H33 = fma(e3z, e3z, fma(e3y, e3y, mul(e3x, e3x)));
+    const double H12 = fma(e1z, e2z, fma(e1y, e2y, mul(e1x, e2x)));
+    const double H13 = fma(e1z, e3z, fma(e1y, e3y, mul(e1x, e3x)));
+    const double H23 = fma(e2z, e3z, fma(e2y, e3y, mul(e2x, e3x)));
     // adj(H) = det(B)^2 * Gram(grad lambda_1..3)
-    const double A11 = fma(H22, H33, -(H23 * H23));
-    const double A22 = fma(H11, H33, -(H13 * H13));
-    const double A33 = fma(H11, H22, -(H12 * H12));
-    const double A12 = fma(H13, H23, -(H12 * H33));
-    const double A13 = fma(H12, H23, -(H13 * H22));
-    const double A23 = fma(H12, H13, -(H11 * H23));
+    const double A11 = fma(H22, H33, -mul(H23, H23));
+    const double A22 = fma(H11, H33, -mul(H13, H13));
+    const double A33 = fma(H11, H22, -mul(H12, H12));
+    const double A12 = fma(H13, H23, -mul(H12, H33));
+    const double A13 = fma(H12, H23, -mul(H13, H22));
+    const double A23 = fma(H12, H13, -mul(H11, H23));
     // det B by the triple product e1 . (e2 x e3): its error grows like cond(B),
     // where det(H) = det(B)^2 from the Gram matrix would grow like cond(B)^2
-    const double cx = fma(e2y, e3z, -(e2z * e3y)), cy = fma(e2z, e3x, -(e2x * e3z)), cz = fma(e2x, e3y, -(e2y * e3x));
-    const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, e1x * cx)));
+    const double cx = fma(e2y, e3z, -mul(e2z, e3y)), cy = fma(e2z, e3x, -mul(e2x, e3z)), cz = fma(e2x, e3y, -mul(e2y, e3x));
+    const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, mul(e1x, cx))));
     const bool bad = not_positive(adet);
     const double r = recip_positive(adet);
-    const double srK = sigmaK * r, srM = sigmaM * r;
+    const double srK = mul(sigmaK, r), srM = mul(sigmaM, r);
 
     // K_kl = (2 sigma / (3|det|)) w_k . w_l
-    const double cK = srK * (2.0 / 3.0);
-    const double h11 = cK * H11, h22 = cK * H22, h33 = cK * H33, h12 = cK * H12, h13 = cK * H13, h23 = cK * H23;
+    const double cK = mul(srK, 2.0 / 3.0);
+    s[0] = mul(cK, H11); s[1] = mul(cK, H22); s[2] = mul(cK, H33);
+    s[3] = mul(cK, H12); s[4] = mul(cK, H13); s[5] = mul(cK, H23);
+    const double cM = mul(srM, 1.0 / 120.0);
+    s[6] = mul(cM, A11); s[7] = mul(cM, A22); s[8] = mul(cM, A33);
+    s[9] = mul(cM, A12); s[10] = mul(cM, A13); s[11] = mul(cM, A23);
+    return bad;
+}
+
+// The 21 + 21 signed entries from h and g: additions and FMAs only.
+__device__ __forceinline__ void ned3_entries(const double (&s)[12], uint32_t neg, double (&Kq)[21], double (&Mq)[21])
+{
+    const double h11 = s[0], h22 = s[1], h33 = s[2], h12 = s[3], h13 = s[4], h23 = s[5];
     const double k03 = h33 - h23, k04 = h13 - h12, k05 = h23 - h22;
     const double k13 = h13 - h33, k14 = h11 - h13, k15 = h12 - h23;
     const double k23 = h23 - h13, k24 = h12 - h11, k25 = h22 - h12;
@@ -162,8 +191,7 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
     // o_j the two other pairs); edges sharing node s with other ends u, v:
     // +-(2 S_s - (p_uv + o(uv))); disjoint edges (a,b), (c,d): p_ad + p_bc -
     // p_ac - p_bd, a difference of two o's. 41 operations after the scaling.
-    const double cM = srM * (1.0 / 120.0);
-    const double g11 = cM * A11, g22 = cM * A22, g33 = cM * A33, g12 = cM * A12, g13 = cM * A13, g23 = cM * A23;
+    const double g11 = s[6], g22 = s[7], g33 = s[8], g12 = s[9], g13 = s[10], g23 = s[11];
     const double p01 = g11 + g12 + g13, p02 = g12 + g22 + g23, p03 = g13 + g23 + g33;   // p12 = -g12, ...
     const double S0 = p01 + p02 + p03;
     const double oA = p01 - g23, oB = p02 - g13, oC = p03 - g12;   // {01,23}, {02,13}, {03,12}
@@ -212,34 +240,46 @@ __device__ __forceinline__ bool ned3_local(const double (&p)[4][3], double sigma
             Kq[q] = flip_if(Kq[q], f);
             Mq[q] = flip_if(Mq[q], f);
         }
-    return bad;
 }
 
 // ---- 3D RT0: 10 + 10 upper entries (DOF k <-> opposite vertex 3-k) ---------
-__device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigmaK, double sigmaM, uint32_t neg,
-                                          double (&Kq)[10], double (&Mq)[10])
+// First part (every product): s = (H11, H22, H33, H12, H13, H23, m20, c0s, q1,
+// q2, q3, kv) in the notation below.
+template <class MUL>
+__device__ __forceinline__ bool rt3_scaled(MUL& mul, const double (&p)[4][3], double sigmaK, double sigmaM,
+                                           double (&s)[12])
 {
     const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
     const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
     const double e3x = p[3][0] - p[0][0], e3y = p[3][1] - p[0][1], e3z = p[3][2] - p[0][2];
-    const double H11 = fma(e1z, e1z, fma(e1y, e1y, e1x * e1x));
-    const double H22 = fma(e2z, e2z, fma(e2y, e2y, e2x * e2x));
-    const double H33 = fma(e3z, e3z, fma(e3y, e3y, e3x * e3x));
-    const double H12 = fma(e1z, e2z, fma(e1y, e2y, e1x * e2x));
-    const double H13 = fma(e1z, e3z, fma(e1y, e3y, e1x * e3x));
-    const double H23 = fma(e2z, e3z, fma(e2y, e3y, e2x * e3x));
-    const double cx = fma(e2y, e3z, -(e2z * e3y)), cy = fma(e2z, e3x, -(e2x * e3z)), cz = fma(e2x, e3y, -(e2y * e3x));
-    const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, e1x * cx)));
+    const double H11 = fma(e1z, e1z, fma(e1y, e1y, mul(e1x, e1x)));
+    const double H22 = fma(e2z, e2z, fma(e2y, e2y, mul(e2x, e2x)));
+    const double H33 = fma(e3z, e3z, fma(e3y, e3y, mul(e3x, e3x)));
+    const double H12 = fma(e1z, e2z, fma(e1y, e2y, mul(e1x, e2x)));
+    const double H13 = fma(e1z, e3z, fma(e1y, e3y, mul(e1x, e3x)));
+    const double H23 = fma(e2z, e3z, fma(e2y, e3y, mul(e2x, e3x)));
+    const double cx = fma(e2y, e3z, -mul(e2z, e3y)), cy = fma(e2z, e3x, -mul(e2x, e3z)), cz = fma(e2x, e3y, -mul(e2y, e3x));
+    const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, mul(e1x, cx))));
     const bool bad = not_positive(adet);
     const double r = recip_positive(adet);
-    const double srK = sigmaK * r, srM = sigmaM * r;
+    const double srK = mul(sigmaK, r), srM = mul(sigmaM, r);
     // M: sigma/(120|det|) [c0 - 5 (S.y_a + S.y_b) + 20 y_a.y_b]
     const double r1 = H11 + H12 + H13, r2 = H12 + H22 + H23, r3 = H13 + H23 + H33;
     const double c0 = (r1 + r2 + r3) + (H11 + H22 + H33);
-    const double cM = srM * (1.0 / 120.0);
-    const double m5 = -5.0 * cM, m20 = 20.0 * cM;
-    const double c0s = c0 * cM;
-    const double q1 = r1 * m5, q2 = r2 * m5, q3 = r3 * m5;
+    const double cM = mul(srM, 1.0 / 120.0);
+    const double m5 = mul(-5.0, cM);
+    s[0] = H11; s[1] = H22; s[2] = H33; s[3] = H12; s[4] = H13; s[5] = H23;
+    s[6] = mul(20.0, cM);
+    s[7] = mul(c0, cM);
+    s[8] = mul(r1, m5); s[9] = mul(r2, m5); s[10] = mul(r3, m5);
+    s[11] = mul(srK, 1.5);   // (div eta)^2 |Khat| = 9/6
+    return bad;
+}
+
+__device__ __forceinline__ void rt3_entries(const double (&s)[12], uint32_t neg, double (&Kq)[10], double (&Mq)[10])
+{
+    const double H11 = s[0], H22 = s[1], H33 = s[2], H12 = s[3], H13 = s[4], H23 = s[5];
+    const double m20 = s[6], c0s = s[7], q1 = s[8], q2 = s[9], q3 = s[10], kv = s[11];
     const double t1 = c0s + q1, t2 = c0s + q2, t3 = c0s + q3;
     // DOF k <-> opposite vertex a = 3 - k; vertex 0 has y_0 = 0
     // (0,0):a=3  (0,1):3,2  (0,2):3,1  (0,3):3,0  (1,1):2  (1,2):2,1  (1,3):2,0  (2,2):1  (2,3):1,0  (3,3):0
@@ -253,7 +293,6 @@ __device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigmaK
     Mq[7] = fma(m20, H11, t1 + q1);
     Mq[8] = t1;
     Mq[9] = c0s;
-    const double kv = srK * 1.5;   // (div eta)^2 |Khat| = 9/6
     int q = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++)
@@ -263,28 +302,56 @@ __device__ __forceinline__ bool rt3_local(const double (&p)[4][3], double sigmaK
             Kq[q] = flip_if(kv, f);
             Mq[q] = flip_if(Mq[q], f);
         }
-    return bad;
 }
 
 // ---- 2D RT0 (VAR 0) and 2D Nedelec (VAR 2): 6 + 6 upper entries ------------
+// First part (every product): RT0 s = (H11, H12, H22, m12, c0s, q1, q2, kv),
+// Nedelec s = (g11, g22, g12, kv) in the notation below.
 template <int VAR>
-__device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigmaK, double sigmaM, uint32_t neg,
-                                          double (&Kq)[6], double (&Mq)[6])
+struct TriScaled {
+    static constexpr int N = VAR == 0 ? 8 : 4;
+};
+
+template <int VAR, class MUL>
+__device__ __forceinline__ bool tri_scaled(MUL& mul, const double (&p)[3][2], double sigmaK, double sigmaM,
+                                           double (&s)[TriScaled<VAR>::N])
 {
     const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1];
     const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1];
-    const double H11 = fma(e1y, e1y, e1x * e1x), H22 = fma(e2y, e2y, e2x * e2x), H12 = fma(e1y, e2y, e1x * e2x);
-    const double adet = abs_bits(fma(e1x, e2y, -(e1y * e2x)));
+    const double H11 = fma(e1y, e1y, mul(e1x, e1x)), H22 = fma(e2y, e2y, mul(e2x, e2x)),
+                 H12 = fma(e1y, e2y, mul(e1x, e2x));
+    const double adet = abs_bits(fma(e1x, e2y, -mul(e1y, e2x)));
     const bool bad = not_positive(adet);
     const double r = recip_positive(adet);
-    const double srK = sigmaK * r, srM = sigmaM * r;
-    const double cM = srM * (1.0 / 24.0);
-    if (VAR == 0) {
+    const double srK = mul(sigmaK, r), srM = mul(sigmaM, r);
+    const double cM = mul(srM, 1.0 / 24.0);
+    const double kv = twice(srK);   // (div eta)^2 |Khat| = 4/2 (RT); curl^2 |Khat| = 4/2 (Ned)
+    if constexpr (VAR == 0) {
         // RT0: sigma/(24|det|) [c0 - 4 (S.y_a + S.y_b) + 12 y_a.y_b], DOF k <-> vertex k
         const double r1 = H11 + H12, r2 = H12 + H22;
         const double c0 = (r1 + r2) + (H11 + H22);
-        const double m4 = -4.0 * cM, m12 = 12.0 * cM;
-        const double c0s = c0 * cM, q1 = r1 * m4, q2 = r2 * m4;
+        const double m4 = mul(-4.0, cM);
+        s[0] = H11; s[1] = H12; s[2] = H22;
+        s[3] = mul(12.0, cM);
+        s[4] = mul(c0, cM);
+        s[5] = mul(r1, m4); s[6] = mul(r2, m4);
+        s[7] = kv;
+    } else {
+        // Nedelec: Whitney forms on edges (1,2), (2,0), (0,1); g = sigma/(24|det|) adj(H)
+        s[0] = mul(cM, H22); s[1] = mul(cM, H11); s[2] = -mul(cM, H12);
+        s[3] = kv;
+    }
+    return bad;
+}
+
+template <int VAR>
+__device__ __forceinline__ void tri_entries(const double (&s)[TriScaled<VAR>::N], uint32_t neg, double (&Kq)[6],
+                                            double (&Mq)[6])
+{
+    double kv;
+    if constexpr (VAR == 0) {
+        const double H11 = s[0], H12 = s[1], H22 = s[2], m12 = s[3], c0s = s[4], q1 = s[5], q2 = s[6];
+        kv = s[7];
         const double t1 = c0s + q1, t2 = c0s + q2;
         Mq[0] = c0s;                          // (0,0)
         Mq[1] = t1;                           // (0,1)
@@ -293,19 +360,17 @@ __device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigmaK
         Mq[4] = fma(m12, H12, t1 + q2);       // (1,2)
         Mq[5] = fma(m12, H22, t2 + q2);       // (2,2)
     } else {
-        // Nedelec: Whitney forms on edges (1,2), (2,0), (0,1); g = sigma/(24|det|) adj(H)
-        const double g11 = cM * H22, g22 = cM * H11, g12 = -(cM * H12);
+        const double g11 = s[0], g22 = s[1], g12 = s[2];
+        kv = s[3];
         const double g01 = -(g11 + g12), g02 = -(g12 + g22);
         const double g00 = -(g01 + g02);
-        double d;
-        d = g11 + g22 - g12; Mq[0] = d + d;
+        Mq[0] = twice(g11 + g22 - g12);
         Mq[1] = fma(-2.0, g01, g02 - g22 + g12);
         Mq[2] = fma(-2.0, g02, g12 - g11 + g01);
-        d = g22 + g00 - g02; Mq[3] = d + d;
+        Mq[3] = twice(g22 + g00 - g02);
         Mq[4] = fma(-2.0, g12, g01 - g00 + g02);
-        d = g00 + g11 - g01; Mq[5] = d + d;
+        Mq[5] = twice(g00 + g11 - g01);
     }
-    const double kv = srK * 2.0;   // (div eta)^2 |Khat| = 4/2 (RT); curl^2 |Khat| = 4/2 (Ned)
     int q = 0;
 #pragma unroll
     for (int k = 0; k < 3; k++)
@@ -315,7 +380,6 @@ __device__ __forceinline__ bool tri_local(const double (&p)[3][2], double sigmaK
             Kq[q] = flip_if(kv, f);
             Mq[q] = flip_if(Mq[q], f);
         }
-    return bad;
 }
 
 }  // namespace ef

@@ -61,8 +61,7 @@ __global__ void __launch_bounds__(TPB) k_element_static(const int32_t* __restric
     const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (e >= T) return;
     double Kq[E::NP], Mq[E::NP];
-    const double sigma = coeff ? __ldg(coeff + e) : 1.0;
-    if (compute_element<VAR>(elems, nodes, sigma, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
+    if (compute_element<VAR>(elems, nodes, coeff, coeff, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
 #pragma unroll
     for (int q = 0; q < E::NP; q++) {
         local[(int64_t)q * T + e] = Kq[q];

@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
             if (e < g.hi) {
                 const double* coeff = nodes0 ? coeff0 : d.coeff;
                 double Kq[E::NP], Mq[E::NP];
-                const double sigma = coeff ? __ldg(coeff + e) : 1.0;
-                if (compute_element<VAR>(d.elems, nodes, sigma, sigma, e, Kq, Mq)) atomicOr(status, ST_DEGENERATE);
+                // FP64 products in the 3D tiles: at the queue's 64 registers the integer
+                // form would spill
+                if (compute_element<VAR, ElemTraits<VAR>::DIM == 2>(d.elems, nodes, coeff, coeff, e, Kq, Mq))
+                    atomicOr(status, ST_DEGENERATE);
 #pragma unroll
                 for (int q = 0; q < E::NP; q++) {
                     const uint32_t p = __ldg(d.inv + (int64_t)q * d.T + e);
