@@ -56,14 +56,19 @@ L2_BYTES = 129 * 1024 * 1024
 # FP64 peak the legs divide by: the probe's measured DFMA rate once the fp64
 # leg has run (run_gpu runs it first), else the nominal figure above
 FP64_PEAK = {"T_ops_per_s": FP64_PEAK_TOPS, "source": "nominal"}
-# FP64 ops per tetrahedron of the adjoint kernel, counted from the source:
-# B 9, H 18, adj(H) 12, det 9, 1/|det| 4 (two Newton steps), r^3 2, a 6,
-# a^T H a 9, Whitney coefficients 17, P 30, <P, A> 6, J 6, A P 27, scale
-# factors 14, Gamma 36, B Gamma 27, node 0 6.
-ADJOINT_FP64_OPS_PER_TET = 9 + 18 + 12 + 9 + 4 + 2 + 6 + 9 + 17 + 30 + 6 + 6 + 27 + 14 + 36 + 27 + 6
+# FP64 arithmetic operations per tetrahedron of the adjoint kernel, counted
+# from the source (csrc/ef_adjoint.cu): B 9, H 18, adj(H) 12, det 9, 1/|det|
+# 4 (two Newton steps), r^3 2, a 6, a^T H a 9, Whitney coefficients 17, P 30,
+# <P, A> 6, J 4, A P 27, scale factors 12, Gamma 36, B Gamma 27, node 0 6,
+# sigma J 1. Its products but the last run on the integer pipes: H 6, adj(H)
+# 6, det 4, r^3 2, a^T H a 4, P 6, <P, A> 1, J 3, A P 9, scale factors 11,
+# Gamma 12, B Gamma 9.
+ADJOINT_FP64_OPS_PER_TET = 9 + 18 + 12 + 9 + 4 + 2 + 6 + 9 + 17 + 30 + 6 + 4 + 27 + 12 + 36 + 27 + 6 + 1
+ADJOINT_INT_PIPE_OPS_PER_TET = 6 + 6 + 4 + 2 + 4 + 6 + 1 + 3 + 9 + 11 + 12 + 9
+ADJOINT_FP64_PIPE_OPS_PER_TET = ADJOINT_FP64_OPS_PER_TET - ADJOINT_INT_PIPE_OPS_PER_TET
 # executed FP64 instructions per tetrahedron of the adjoint kernel (ncu sass
-# counters on the 24^3 cube: 43 DADD, 144 DFMA, 74 DMUL)
-ADJOINT_FP64_EXECUTED_PER_TET = 261
+# counters on the 24^3 cube: 39 DADD, 123 DFMA, 1 DMUL)
+ADJOINT_FP64_EXECUTED_PER_TET = 163
 # DRAM bytes (read + write) per element of the Nedelec-3D element kernel of
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
 # on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
@@ -171,12 +176,13 @@ class ClockSampler:
 # sm__sass_thread_inst_executed_op_{dadd,dfma,dmul}_pred_on.sum of one launch
 # divided by its elements; every FP64 warp instruction had all 32 lanes on):
 # (kind, dim) -> DADD, DFMA, DMUL. Measured on the 24^3 cube (3D) and the
-# level-5 L-shape (2D); the counts do not depend on the mesh.
+# level-5 L-shape (2D); the counts do not depend on the mesh. No DMUL: the
+# products run on the integer pipes.
 ELEMENT_KERNEL_FP64_EXECUTED = {
-    (2, 3): {"dadd": 53, "dfma": 45, "dmul": 32},
-    (1, 3): {"dadd": 20, "dfma": 36, "dmul": 17},
-    (1, 2): {"dadd": 9, "dfma": 17, "dmul": 10},
-    (2, 2): {"dadd": 17, "dfma": 17, "dmul": 9},
+    (2, 3): {"dadd": 47, "dfma": 45, "dmul": 0},
+    (1, 3): {"dadd": 29, "dfma": 27, "dmul": 0},
+    (1, 2): {"dadd": 14, "dfma": 11, "dmul": 0},
+    (2, 2): {"dadd": 20, "dfma": 11, "dmul": 0},
 }
 ELEMENT_KERNEL_FP64_MIX = ELEMENT_KERNEL_FP64_EXECUTED[(2, 3)]
 
@@ -216,9 +222,11 @@ def run_fp64_probe(gpu_index: int) -> dict:
 
 
 def fp64_ops_per_element(kind: int, dim: int) -> int:
-    """FP64 pipe operations (DADD, DMUL, DFMA each 1) of one element's local
-    matrices in the closed forms of csrc/ef_element.cuh, counted from the
-    source; the reciprocal 1/|det| is two Newton steps, 4 DFMA."""
+    """FP64 arithmetic operations (add, multiply, FMA each 1) of one element's
+    local matrices in the closed forms of csrc/ef_element.cuh, counted from the
+    source; the reciprocal 1/|det| is two Newton steps, 4 FMA. In the element
+    kernels the products (and the exact doublings) run on the integer pipes
+    (INT_PIPE_OPS_PER_ELEMENT), the rest on the FP64 pipe."""
     if (kind, dim) == (2, 3):
         # B 9, H 18, adj(H) 12, det 9, 1/|det| 4, sigma*r 2, K: 1 + 6 + 15, M: 1 + 6 + 41
         return 9 + 18 + 12 + 9 + 4 + 2 + 22 + 48
@@ -230,6 +238,23 @@ def fp64_ops_per_element(kind: int, dim: int) -> int:
         return 4 + 6 + 2 + 4 + 2 + 1 + 2 + 3 + 2 + 3 + 2 + 6 + 1
     # 2D Nedelec: B 4, H 6, det 2, 1/|det| 4, sigma*r 2, cM 1, g 3, g01 g02 2, g00 1, entries 18, K 1
     return 4 + 6 + 2 + 4 + 2 + 1 + 3 + 2 + 1 + 18 + 1
+
+
+# Of those, the operations that the two-pass element kernel runs on the
+# integer pipes (csrc/ef_intmul.cuh, bit for bit the FP64 results): every
+# product, and in 2D the exact doublings 2 sigma/|det| (and in 2D Nedelec the
+# three doubled diagonal sums), which had been FP64 instructions.
+INT_PIPE_OPS_PER_ELEMENT = {
+    (2, 3): 6 + 6 + 3 + 1 + 2 + 1 + 6 + 1 + 6,   # H, adj(H), cross, det, sigma*r, cK, h, cM, g: 32
+    (1, 3): 6 + 3 + 1 + 2 + 1 + 2 + 1 + 3 + 1,   # H, cross, det, sigma*r, cM, m5 m20, c0s, q, kv: 20
+    (1, 2): 3 + 1 + 2 + 1 + 2 + 1 + 2 + 1,       # H, det, sigma*r, cM, m4 m12, c0s, q, kv: 13
+    (2, 2): 3 + 1 + 2 + 1 + 3 + 1 + 3,           # H, det, sigma*r, cM, g, kv, diagonals: 14
+}
+
+
+def fp64_pipe_ops_per_element(kind: int, dim: int) -> int:
+    """Operations of fp64_ops_per_element that stay on the FP64 pipe."""
+    return fp64_ops_per_element(kind, dim) - INT_PIPE_OPS_PER_ELEMENT[(kind, dim)]
 
 
 def run_reference(args):
@@ -432,12 +457,17 @@ def run_batched(args, dev, plain_rate):
 
 def _fp64_leg(kind: int, dim: int, T: int, ms: float) -> dict:
     """An element kernel's launch against the FP64 pipe peak: by the source
-    count (the algorithmic operations) and by the executed instructions."""
-    src, exe = fp64_ops_per_element(kind, dim), fp64_executed_per_element(kind, dim)
+    count of the operations on that pipe and by the executed FP64
+    instructions; beside them all FP64 operations of the routine (products
+    included, which run on the integer pipes) per second."""
+    src, exe = fp64_pipe_ops_per_element(kind, dim), fp64_executed_per_element(kind, dim)
+    tot = fp64_ops_per_element(kind, dim)
     peak = FP64_PEAK["T_ops_per_s"]
     a_src, a_exe = src * T / (ms / 1e3) / 1e12, exe * T / (ms / 1e3) / 1e12
-    return {"ops_per_elem": src, "achieved": a_src, "peak": peak, "unit": "T fp64-ops/s", "frac": a_src / peak,
+    return {"ops_per_elem": src, "achieved": a_src, "peak": peak, "unit": "T fp64-pipe-ops/s", "frac": a_src / peak,
             "executed_per_elem": exe, "achieved_executed": a_exe, "frac_executed": a_exe / peak,
+            "all_fp64_ops_per_elem": tot, "int_pipe_ops_per_elem": INT_PIPE_OPS_PER_ELEMENT[(kind, dim)],
+            "all_fp64_ops_T_per_s": tot * T / (ms / 1e3) / 1e12,
             "ms_per_launch": ms, "peak_source": FP64_PEAK["source"]}
 
 
@@ -739,13 +769,16 @@ def run_adjoint(args, dev):
     ms_asm = timed(lambda: ef.ef_assemble(plan.handle, tn, tc, K, M, stream), args.adjoint_steps)
     plan.check()
     T = elems.shape[0]
-    ops = ADJOINT_FP64_OPS_PER_TET * T
+    ops = ADJOINT_FP64_PIPE_OPS_PER_TET * T
     out = {"value": T / (ms_adj / 1e3) / 1e6, "unit": UNIT, "workload": f"ned3d_kuhn{args.adjoint_cube}_jitter0.2",
            "elements": int(T), "ms_per_step": ms_adj,
            "plain_same_mesh": {"value": T / (ms_asm / 1e3) / 1e6, "ms_per_step": ms_asm},
            "vs_plain": ms_asm / ms_adj,
-           "fp64": {"ops_per_elem": ADJOINT_FP64_OPS_PER_TET, "achieved": ops / (ms_adj / 1e3) / 1e12,
-                    "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-ops/s",
+           "fp64": {"ops_per_elem": ADJOINT_FP64_PIPE_OPS_PER_TET, "achieved": ops / (ms_adj / 1e3) / 1e12,
+                    "peak": FP64_PEAK["T_ops_per_s"], "unit": "T fp64-pipe-ops/s",
+                    "all_fp64_ops_per_elem": ADJOINT_FP64_OPS_PER_TET,
+                    "int_pipe_ops_per_elem": ADJOINT_INT_PIPE_OPS_PER_TET,
+                    "all_fp64_ops_T_per_s": ADJOINT_FP64_OPS_PER_TET * T / (ms_adj / 1e3) / 1e12,
                     "frac": ops / (ms_adj / 1e3) / 1e12 / FP64_PEAK["T_ops_per_s"],
                     "peak_source": FP64_PEAK["source"],
                     "executed_per_elem": ADJOINT_FP64_EXECUTED_PER_TET,
@@ -939,7 +972,8 @@ def run_gpu(args):
     info = plan.info()
     U = info["n_upper"]
     n_pairs = info["n_contrib"] // T
-    elem_ops = T * fp64_ops_per_element(w["kind"], w["dim"])
+    elem_ops = T * fp64_pipe_ops_per_element(w["kind"], w["dim"])
+    elem_ops_all = T * fp64_ops_per_element(w["kind"], w["dim"])
     sum_ops = 2 * (T * n_pairs - U)
     sum_bytes = 2 * n_pairs * 8 * T + 14 * U + 16 * nnz   # list, indices + store orders, CSR values
     if k_calls > 0 and info["fused_block"] == 0 and info["assemble_launches"] == 2:
@@ -961,7 +995,7 @@ def run_gpu(args):
     peak = probe["peak_T_ops_per_s"]
     exec_ops = sum(ELEMENT_KERNEL_FP64_MIX.values()) * T if dom_ops == elem_ops else None
     roofline = {
-        "bound": "alu", "unit": "T fp64-ops/s", "achieved": achieved_ops, "peak": peak,
+        "bound": "alu", "unit": "T fp64-pipe-ops/s", "achieved": achieved_ops, "peak": peak,
         "frac": achieved_ops / peak, "traffic": traffic,
         "peak_source": ("measured (bench fp64 leg: ef_fp64_probe DFMA lane-ops/s on this GPU, "
                         f"median SM clock {probe['clocks'].get('sm_mhz')} MHz during the probe)"
@@ -970,7 +1004,13 @@ def run_gpu(args):
         "peak_nominal_source": f"{SMS} SMs x {FP64_PER_CLK_PER_SM} FP64 ops/clk/SM x {SM_MAX_MHZ} MHz",
         "kernel": dom_name, "ms_per_launch": dom_ms,
         "fp64_ops_per_launch": int(dom_ops), "fp64_ops_per_elem": dom_ops / T,
-        "fp64_ops_source": "counted from the source (csrc/ef_element.cuh)",
+        "fp64_ops_source": ("counted from the source (csrc/ef_element.cuh): the operations on the FP64 pipe; "
+                            "the products run on the integer pipes (csrc/ef_intmul.cuh)"),
+        "all_fp64_ops": (None if dom_ops != elem_ops else
+                         {"per_elem": elem_ops_all / T,
+                          "int_pipe_per_elem": INT_PIPE_OPS_PER_ELEMENT[(w["kind"], w["dim"])],
+                          "T_per_s": elem_ops_all / (dom_ms / 1e3) / 1e12,
+                          "of_fp64_pipe_peak": elem_ops_all / (dom_ms / 1e3) / 1e12 / peak}),
         "executed": (None if exec_ops is None else
                      {"fp64_ops_per_elem": exec_ops / T, "source": "ncu sass FP64 instruction counters",
                       "achieved": exec_ops / (dom_ms / 1e3) / 1e12,

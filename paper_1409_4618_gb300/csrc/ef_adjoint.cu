@@ -29,7 +29,129 @@ namespace {
 
 constexpr int ADJ_TPB = 256;
 
-__global__ void __launch_bounds__(ADJ_TPB, 3) k_adjoint_ned3(const int32_t* __restrict__ elems,
+// One element: J1 = u~^T K^ u~ + v~^T M^ v~ with the coefficient left out (the
+// element's energy is sigma J1) and 2 sigma (B Gamma) column by column into
+// gcol (node i+1 gets column i). MUL forms every product (IntMul on the
+// integer pipes, or FpMul): no product is contracted into an FMA, so both give
+// the same bits.
+template <class MUL>
+__device__ __forceinline__ void adjoint_element(MUL& mul, const double (&p)[4][3], double sigma, const double (&ut)[6],
+                                                const double (&vt)[6], bool& degenerate, double& J1,
+                                                double (&gcol)[3][3])
+{
+    double B[3][3];   // B[row][col], col i = e_{i+1}
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) B[c][i] = p[i + 1][c] - p[0][c];
+    double H[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            H[i][j] = fma(B[2][i], B[2][j], fma(B[1][i], B[1][j], mul(B[0][i], B[0][j])));
+            H[j][i] = H[i][j];
+        }
+    double A[3][3];
+    A[0][0] = fma(H[1][1], H[2][2], -mul(H[1][2], H[1][2]));
+    A[1][1] = fma(H[0][0], H[2][2], -mul(H[0][2], H[0][2]));
+    A[2][2] = fma(H[0][0], H[1][1], -mul(H[0][1], H[0][1]));
+    A[0][1] = A[1][0] = fma(H[0][2], H[1][2], -mul(H[0][1], H[2][2]));
+    A[0][2] = A[2][0] = fma(H[0][1], H[1][2], -mul(H[0][2], H[1][1]));
+    A[1][2] = A[2][1] = fma(H[0][1], H[0][2], -mul(H[0][0], H[1][2]));
+    // det B by the triple product (error ~ cond(B) eps)
+    const double cx = fma(B[1][1], B[2][2], -mul(B[2][1], B[1][2]));
+    const double cy = fma(B[2][1], B[0][2], -mul(B[0][1], B[2][2]));
+    const double cz = fma(B[0][1], B[1][2], -mul(B[1][1], B[0][2]));
+    const double adet = abs_bits(fma(B[2][0], cz, fma(B[1][0], cy, mul(B[0][0], cx))));
+    degenerate = not_positive(adet);
+    const double r = recip_positive(adet);
+    const double r3 = mul(mul(r, r), r);
+
+    // K part: aHa = a^T H a over the symmetric H
+    const double av[3] = {ut[1] - ut[2] + ut[4], ut[2] - ut[0] + ut[5], ut[0] - ut[1] + ut[3]};
+    const double aHa = fma(av[0], fma(H[0][0], av[0], twice(fma(H[0][1], av[1], mul(H[0][2], av[2])))),
+                           fma(av[1], fma(H[1][1], av[1], twice(mul(H[1][2], av[2]))), mul(av[2], mul(H[2][2], av[2]))));
+
+    // M part: C antisymmetric over the 4 nodes, edges (0,1),(0,2),(0,3),(1,2),(2,3),(3,1)
+    const double c0 = -(vt[0] + vt[1] + vt[2]);
+    const double c1 = vt[0] - vt[3] + vt[5];
+    const double c2 = vt[1] + vt[3] - vt[4];
+    const double c3 = vt[2] + vt[4] - vt[5];
+    const double beta[3] = {c1 - c0, c2 - c0, c3 - c0};
+    // D = C S: row k, column j (node j+1): C_k,j+1 - C_k,0
+    const double D[4][3] = {{vt[0], vt[1], vt[2]},
+                            {vt[0], vt[3] + vt[0], vt[0] - vt[5]},
+                            {vt[1] - vt[3], vt[1], vt[4] + vt[1]},
+                            {vt[5] + vt[2], vt[2] - vt[4], vt[2]}};
+    double P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            double s = mul(beta[i], beta[j]);
+#pragma unroll
+            for (int k = 0; k < 4; k++) s = fma(D[k][i], D[k][j], s);
+            P[i][j] = s;
+            P[j][i] = s;
+        }
+    // <P, A> over the symmetric pair
+    const double PA = fma(P[0][0], A[0][0], fma(P[1][1], A[1][1], fma(P[2][2], A[2][2],
+                          twice(fma(P[0][1], A[0][1], fma(P[0][2], A[0][2], mul(P[1][2], A[1][2])))))));
+
+    // J1 = (2/3) r aHa + (r/120) PA
+    J1 = fma(mul(r, 2.0 / 3.0), aHa, mul(mul(r, 1.0 / 120.0), PA));
+
+    // 2 sigma Gamma, Gamma = (2/3)(r a a^T - r^3/2 aHa A) + r^3/120 (PA/2 A - A P A),
+    // symmetric: six entries; A P A from the full A P and the upper half of (A P) A
+    double AP[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) AP[i][j] = fma(A[i][2], P[2][j], fma(A[i][1], P[1][j], mul(A[i][0], P[0][j])));
+    const double s2 = twice(sigma);
+    const double kA = mul(s2, fma(mul(r3, -1.0 / 3.0), aHa, mul(mul(r3, 1.0 / 240.0), PA)));
+    const double kAPA = mul(s2, mul(r3, -1.0 / 120.0));
+    const double kaa = mul(s2, mul(r, 2.0 / 3.0));
+    const double ka[3] = {mul(kaa, av[0]), mul(kaa, av[1]), mul(kaa, av[2])};
+    double Gm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            const double apa = fma(AP[i][2], A[2][j], fma(AP[i][1], A[1][j], mul(AP[i][0], A[0][j])));
+            Gm[i][j] = fma(kAPA, apa, fma(kA, A[i][j], mul(ka[i], av[j])));
+            Gm[j][i] = Gm[i][j];
+        }
+    // dJ/de_i = 2 sigma (B Gamma)[:, i]
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) gcol[i][c] = fma(B[c][2], Gm[2][i], fma(B[c][1], Gm[1][i], mul(B[c][0], Gm[0][i])));
+}
+
+__device__ __forceinline__ void adjoint_load(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
+                                             const double* __restrict__ coeff, const int32_t* __restrict__ e2d,
+                                             const double* __restrict__ u, const double* __restrict__ v, int64_t e,
+                                             double (&p)[4][3], double& sigma, double (&ut)[6], double (&vt)[6])
+{
+    int32_t g[4];
+    load_ids<NED3>(elems, e, g);
+    const uint32_t neg = sign_bits<NED3>(g);
+    load_coords<NED3>(nodes, g, p);
+    sigma = coeff ? __ldg(coeff + e) : 1.0;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const int32_t d = __ldg(e2d + e * 6 + k);
+        ut[k] = flip_if(__ldg(u + d), neg >> k);
+        vt[k] = flip_if(__ldg(v + d), neg >> k);
+    }
+}
+
+// The products on the integer pipes (IntMul); an element in which an operand
+// or a product leaves the normal numbers and zero is repeated with the FP64
+// multiply from its data loaded again, which gives the same bits.
+__global__ void __launch_bounds__(ADJ_TPB, 2) k_adjoint_ned3(const int32_t* __restrict__ elems,
                                                           const double* __restrict__ nodes,
                                                           const double* __restrict__ coeff,
                                                           const int32_t* __restrict__ e2d,
@@ -42,118 +164,34 @@ __global__ void __launch_bounds__(ADJ_TPB, 3) k_adjoint_ned3(const int32_t* __re
     const int64_t e = (int64_t)blockIdx.x * ADJ_TPB + threadIdx.x;
     double Jloc = 0.0;
     if (e < T) {
-        int32_t g[4];
-        load_ids<NED3>(elems, e, g);
-        const uint32_t neg = sign_bits<NED3>(g);
-        double p[4][3];
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) p[a][c] = __ldg(nodes + (int64_t)g[a] * 3 + c);
-        const double sigma = coeff ? __ldg(coeff + e) : 1.0;
-        double ut[6], vt[6];
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-            const int32_t d = __ldg(e2d + e * 6 + k);
-            ut[k] = flip_if(__ldg(u + d), neg >> k);
-            vt[k] = flip_if(__ldg(v + d), neg >> k);
+        double J1, gcol[3][3], sigma;
+        bool degenerate;
+        {
+            double p[4][3], ut[6], vt[6];
+            adjoint_load(elems, nodes, coeff, e2d, u, v, e, p, sigma, ut, vt);
+            IntMul im;
+            adjoint_element(im, p, sigma, ut, vt, degenerate, J1, gcol);
+            if (im.off) {
+                // the index through an opaque move: the loads are not merged with the ones above
+                int64_t e2 = e;
+                asm volatile("" : "+l"(e2));
+                adjoint_load(elems, nodes, coeff, e2d, u, v, e2, p, sigma, ut, vt);
+                FpMul fm;
+                adjoint_element(fm, p, sigma, ut, vt, degenerate, J1, gcol);
+            }
         }
-        double B[3][3];   // B[row][col], col i = e_{i+1}
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) B[c][i] = p[i + 1][c] - p[0][c];
-        double H[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = i; j < 3; j++) {
-                H[i][j] = fma(B[2][i], B[2][j], fma(B[1][i], B[1][j], B[0][i] * B[0][j]));
-                H[j][i] = H[i][j];
-            }
-        double A[3][3];
-        A[0][0] = fma(H[1][1], H[2][2], -(H[1][2] * H[1][2]));
-        A[1][1] = fma(H[0][0], H[2][2], -(H[0][2] * H[0][2]));
-        A[2][2] = fma(H[0][0], H[1][1], -(H[0][1] * H[0][1]));
-        A[0][1] = A[1][0] = fma(H[0][2], H[1][2], -(H[0][1] * H[2][2]));
-        A[0][2] = A[2][0] = fma(H[0][1], H[1][2], -(H[0][2] * H[1][1]));
-        A[1][2] = A[2][1] = fma(H[0][1], H[0][2], -(H[0][0] * H[1][2]));
-        // det B by the triple product (error ~ cond(B) eps)
-        const double cx = fma(B[1][1], B[2][2], -(B[2][1] * B[1][2]));
-        const double cy = fma(B[2][1], B[0][2], -(B[0][1] * B[2][2]));
-        const double cz = fma(B[0][1], B[1][2], -(B[1][1] * B[0][2]));
-        const double adet = abs_bits(fma(B[2][0], cz, fma(B[1][0], cy, B[0][0] * cx)));
-        if (not_positive(adet)) atomicOr(status, ST_DEGENERATE);
-        const double r = recip_positive(adet);
-        const double r3 = r * r * r;
-
-        // K part: aHa = a^T H a over the symmetric H
-        const double av[3] = {ut[1] - ut[2] + ut[4], ut[2] - ut[0] + ut[5], ut[0] - ut[1] + ut[3]};
-        const double aHa = fma(av[0], fma(H[0][0], av[0], twice(fma(H[0][1], av[1], H[0][2] * av[2]))),
-                               fma(av[1], fma(H[1][1], av[1], twice(H[1][2] * av[2])), av[2] * (H[2][2] * av[2])));
-
-        // M part: C antisymmetric over the 4 nodes, edges (0,1),(0,2),(0,3),(1,2),(2,3),(3,1)
-        const double c0 = -(vt[0] + vt[1] + vt[2]);
-        const double c1 = vt[0] - vt[3] + vt[5];
-        const double c2 = vt[1] + vt[3] - vt[4];
-        const double c3 = vt[2] + vt[4] - vt[5];
-        const double beta[3] = {c1 - c0, c2 - c0, c3 - c0};
-        // D = C S: row k, column j (node j+1): C_k,j+1 - C_k,0
-        const double D[4][3] = {{vt[0], vt[1], vt[2]},
-                                {vt[0], vt[3] + vt[0], vt[0] - vt[5]},
-                                {vt[1] - vt[3], vt[1], vt[4] + vt[1]},
-                                {vt[5] + vt[2], vt[2] - vt[4], vt[2]}};
-        double P[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = i; j < 3; j++) {
-                double s = beta[i] * beta[j];
-#pragma unroll
-                for (int k = 0; k < 4; k++) s = fma(D[k][i], D[k][j], s);
-                P[i][j] = s;
-                P[j][i] = s;
-            }
-        // <P, A> over the symmetric pair
-        const double PA = fma(P[0][0], A[0][0], fma(P[1][1], A[1][1], fma(P[2][2], A[2][2],
-                              twice(fma(P[0][1], A[0][1], fma(P[0][2], A[0][2], P[1][2] * A[1][2]))))));
-
-        const double J1 = (2.0 / 3.0) * r * aHa + (r / 120.0) * PA;
+        if (degenerate) atomicOr(status, ST_DEGENERATE);
         if (gcoeff) gcoeff[e] = J1;
-        Jloc = sigma * J1;
-
-        // 2 sigma Gamma, Gamma = (2/3)(r a a^T - r^3/2 aHa A) + r^3/120 (PA/2 A - A P A),
-        // symmetric: six entries; A P A from the full A P and the upper half of (A P) A
-        double AP[3][3];
+        Jloc = __dmul_rn(sigma, J1);
+        // node 0 gets minus the sum of the other three
+        double g0[3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) AP[i][j] = fma(A[i][2], P[2][j], fma(A[i][1], P[1][j], A[i][0] * P[0][j]));
-        const double s2 = 2.0 * sigma;
-        const double kA = s2 * (-(1.0 / 3.0) * r3 * aHa + (r3 / 240.0) * PA);
-        const double kAPA = s2 * -(r3 / 120.0);
-        const double kaa = s2 * (2.0 / 3.0) * r;
-        const double ka[3] = {kaa * av[0], kaa * av[1], kaa * av[2]};
-        double Gm[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = i; j < 3; j++) {
-                const double apa = fma(AP[i][2], A[2][j], fma(AP[i][1], A[1][j], AP[i][0] * A[0][j]));
-                Gm[i][j] = fma(kAPA, apa, fma(kA, A[i][j], ka[i] * av[j]));
-                Gm[j][i] = Gm[i][j];
-            }
-        // dJ/de_i = 2 sigma (B Gamma)[:, i]; node 0 gets minus the sum
-        double g0[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const double gi = fma(B[c][2], Gm[2][i], fma(B[c][1], Gm[1][i], B[c][0] * Gm[0][i]));
-                gpart[(e * 4 + i + 1) * 3 + c] = gi;
-                g0[c] = i == 0 ? -gi : g0[c] - gi;
+                gpart[(e * 4 + i + 1) * 3 + c] = gcol[i][c];
+                g0[c] = i == 0 ? -gcol[i][c] : g0[c] - gcol[i][c];
             }
-        }
 #pragma unroll
         for (int c = 0; c < 3; c++) gpart[(e * 4) * 3 + c] = g0[c];
     }
