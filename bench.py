@@ -197,12 +197,14 @@ def run_fp64_probe(gpu_index: int) -> dict:
     (ef_fp64_probe: independent chains of one operation on every SM) for DFMA,
     DADD and DMUL, three launches each, with the SM clock sampled meanwhile.
     The DFMA rate is the peak of the element kernels' roofline; the rate for
-    the element kernel's own instruction mix is reported beside it."""
+    the element kernel's own instruction mix is reported beside it. Also the
+    integer-pipe multiply alone and in half of the chains beside DFMA in the
+    other half (the two pipes at once)."""
     from paper_1409_4618_gb300 import edgefem as ef
 
     rates = {}
     with ClockSampler(gpu_index) as clk:
-        for name, op in (("dfma", 0), ("dadd", 1), ("dmul", 2)):
+        for name, op in (("dfma", 0), ("dadd", 1), ("dmul", 2), ("int_mul", 3), ("dfma_and_int_mul", 4)):
             best = None
             for _ in range(3):
                 r, ms = ef.ef_fp64_probe(op, FP64_PROBE_ITERS)
@@ -213,7 +215,7 @@ def run_fp64_probe(gpu_index: int) -> dict:
     mhz = clocks.get("sm_mhz")
     for v in rates.values():
         v["ops_per_clk_per_sm"] = v["ops_per_s"] / (SMS * mhz * 1e6) if mhz else None
-    mix = ELEMENT_KERNEL_FP64_MIX
+    mix = {k: v for k, v in ELEMENT_KERNEL_FP64_MIX.items() if v}
     t_mix = sum(mix[k] / rates[k]["ops_per_s"] for k in mix)
     return {"rates": rates, "clocks": clocks, "peak_T_ops_per_s": rates["dfma"]["T_ops_per_s"],
             "element_mix_T_ops_per_s": sum(mix.values()) / t_mix / 1e12, "element_mix": mix,

@@ -478,7 +478,10 @@ void ef_csr_free(ef_csr* csr);
  * ef_fp64_probe -- not part of the paper's method: measures the throughput of
  * this GPU's FP64 pipe, the bound of the element kernels (their work is a
  * stream of FP64 additions, multiplications and fused multiply-adds, see
- * Sec. 2.4's local matrices). op = 0: DFMA, 1: DADD, 2: DMUL. Every thread
+ * Sec. 2.4's local matrices). op = 0: DFMA, 1: DADD, 2: DMUL, 3: the
+ * integer-pipe multiply of the element kernels (bit for bit DMUL), 4: DFMA in
+ * half of the chains and the integer-pipe multiply in the other half (both
+ * pipes at once). Every thread
  * of a grid of 4 CTAs of 256 threads per SM runs 8 independent chains of
  * `iters` operations (rounded up to a multiple of 8); *ops_per_s receives the lane operations per second
  * (one per DFMA), *ms (may be NULL) the timed launch's duration. d_sink: one
@@ -487,6 +490,22 @@ void ef_csr_free(ef_csr* csr);
  * Errors: EF_ERR_ARG, EF_ERR_CUDA.
  */
 int ef_fp64_probe(int op, int64_t iters, double* d_sink, double* ops_per_s, double* ms, void* stream);
+
+/*
+ * ef_int_mul_check -- not part of the paper's method: checks the integer-pipe
+ * FP64 multiply that the element and adjoint kernels use for their products
+ * against the FP64 multiply instruction. Generates n operand pairs from
+ * SplitMix64(seed, index) (random significands and signs; exponents over the
+ * whole range, near the bias, and significands with many trailing zeros;
+ * special values: zero, subnormals, infinity, NaN, the extreme normals),
+ * multiplies each both ways and counts into the caller's device buffer
+ * d_counts[2] (unsigned 64-bit): [0] pairs the integer form hands back to the
+ * FP64 instruction (an operand or the product outside the normal numbers and
+ * zero), [1] the other pairs whose bits differ (0 when correct). Clears
+ * d_counts and launches on `stream`; does not synchronise. Errors: EF_ERR_ARG
+ * (n < 0, NULL d_counts), EF_ERR_CUDA.
+ */
+int ef_int_mul_check(int64_t n, uint64_t seed, unsigned long long* d_counts, void* stream);
 
 /* ---- diagnostics ------------------------------------------------------------ */
 

@@ -130,6 +130,7 @@ def load():
             "ef_load_vector": ([P, P, I, P, P, P], I),
             "ef_load_derivative": ([P, P, I, P, P, P], I),
             "ef_fp64_probe": ([I, I64, P, C.POINTER(C.c_double), C.POINTER(C.c_double), P], I),
+            "ef_int_mul_check": ([I64, C.c_uint64, P, P], I),
             "ef_status_string": ([I], C.c_char_p),
             "ef_last_error": ([], C.c_char_p),
         }
@@ -247,12 +248,24 @@ def ef_adjoint(plan, nodes, coeff, u, v, J=None, grad_nodes=None, grad_coeff=Non
 
 
 def ef_fp64_probe(op: int, iters: int, stream=None) -> tuple[float, float]:
-    """(lane operations per second, ms) of the FP64 pipe for op 0 = DFMA, 1 = DADD, 2 = DMUL."""
+    """(lane operations per second, ms) for op 0 = DFMA, 1 = DADD, 2 = DMUL,
+    3 = the integer-pipe multiply, 4 = DFMA and the integer-pipe multiply in
+    half of the chains each."""
     sink = torch.zeros(1, dtype=torch.float64, device="cuda")
     rate, ms = C.c_double(), C.c_double()
     _check(load().ef_fp64_probe(int(op), int(iters), C.c_void_p(sink.data_ptr()), C.byref(rate), C.byref(ms),
                                 _stream_ptr(stream)))
     return rate.value, ms.value
+
+
+def ef_int_mul_check(n: int, seed: int, stream=None) -> tuple[int, int]:
+    """(pairs handed to the FP64 instruction, mismatching pairs) of the
+    integer-pipe multiply against the FP64 multiply on n generated pairs."""
+    counts = torch.zeros(2, dtype=torch.int64, device="cuda")
+    _check(load().ef_int_mul_check(int(n), C.c_uint64(int(seed) & (2**64 - 1)), C.c_void_p(counts.data_ptr()),
+                                   _stream_ptr(stream)))
+    flagged, mismatched = counts.cpu().tolist()
+    return flagged, mismatched
 
 
 def ef_plan_check(plan, stream=None):
