@@ -73,7 +73,7 @@ ADJOINT_FP64_EXECUTED_PER_TET = 163
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
 # on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
 # to the elements.
-ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (75.725056e6 + 166.208000e6) / 663552
+ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (74.955520e6 + 176.536064e6) / 663552
 
 
 def _peaks():
@@ -473,6 +473,47 @@ def _fp64_leg(kind: int, dim: int, T: int, ms: float) -> dict:
             "ms_per_launch": ms, "peak_source": FP64_PEAK["source"]}
 
 
+def _timed_calls(torch, fn, steps, stream) -> float:
+    """ms per call of fn, CUDA events on the launching stream around `steps`
+    calls (no per-call events inside the timed region)."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _kernel_split(ef, plan, fn, steps):
+    """Per-kernel ms of ef_assemble from the library's own events
+    (ef_plan_profile), recorded over `steps` further calls outside the timed
+    region: their three event records per call would add host time to
+    launch-bound calls."""
+    plan.profile(steps)
+    for _ in range(steps):
+        fn()
+    k1, k2, calls = plan.profile_read()
+    plan.profile(0)
+    return k1, k2, calls
+
+
+def _two_pass_ms(ef, torch, plan, tn, tc, K, M, steps, stream) -> float:
+    """ms per call of the two-pass schedule (ef_assemble_two_pass) on the same
+    buffers, CUDA events on the launching stream: the tuned schedule's
+    comparison."""
+    for _ in range(3):
+        ef.ef_assemble_two_pass(plan.handle, tn, tc, K, M, stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ef.ef_assemble_two_pass(plan.handle, tn, tc, K, M, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    return a.elapsed_time(b) / steps
+
+
 def run_rt0(args, dev, peaks):
     """The two RT0 workloads: 3D RT0 on the 128^3 cube (12,582,912 tets,
     jitter 0.2h seed 3, log-uniform coefficient; the large, memory-heavy case)
@@ -503,16 +544,9 @@ def run_rt0(args, dev, peaks):
         for _ in range(3):
             ef.ef_assemble(plan.handle, tn, tc, K, M, stream)
         torch.cuda.synchronize()
-        plan.profile(steps)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(steps):
-            ef.ef_assemble(plan.handle, tn, tc, K, M, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / steps
-        k1, k2, calls = plan.profile_read()
-        plan.profile(0)
+        call = lambda: ef.ef_assemble(plan.handle, tn, tc, K, M, stream)
+        ms = _timed_calls(torch, call, steps, stream)
+        k1, k2, calls = _kernel_split(ef, plan, call, steps)
         plan.check()
         T, V, nnz = elems.shape[0], nodes.shape[0], plan.nnz
         alg = (4 * (dim + 1) + (0 if coeff is None else 8)) * T + 8 * dim * V + 16 * nnz
@@ -525,6 +559,9 @@ def run_rt0(args, dev, peaks):
         if tuned == 0 and calls:
             # the element kernel of the two-pass schedule against the FP64 pipe
             out[name]["fp64_element_kernel"] = _fp64_leg(1, dim, T, k1 / calls)
+        else:
+            tp = _two_pass_ms(ef, torch, plan, tn, tc, K, M, steps, stream)
+            out[name]["two_pass"] = {"ms_per_step": tp, "tuned_speedup": tp / ms}
         plan.close()
         del K, M
         torch.cuda.empty_cache()
@@ -557,18 +594,11 @@ def run_lshape(args, dev, peaks):
         for _ in range(3):
             ef.ef_assemble(plan.handle, tn, None, K, M, stream)
         torch.cuda.synchronize()
-        plan.profile(steps)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        call = lambda: ef.ef_assemble(plan.handle, tn, None, K, M, stream)
         _nvtx(torch, "timed")
-        a.record(stream)
-        for _ in range(steps):
-            ef.ef_assemble(plan.handle, tn, None, K, M, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
+        ms = _timed_calls(torch, call, steps, stream)
         _nvtx(torch, None)
-        ms = a.elapsed_time(b) / steps
-        k1, k2, calls = plan.profile_read()
-        plan.profile(0)
+        k1, k2, calls = _kernel_split(ef, plan, call, steps)
         plan.check()
         alg = 12 * T + 16 * V + 16 * plan.nnz
         gbs = alg / (ms / 1e3) / 1e9
@@ -579,6 +609,9 @@ def run_lshape(args, dev, peaks):
                        "algorithmic_bytes_per_step": int(alg), "bytes_per_elem": alg / T}}
         if tuned == 0 and calls:
             leg["fp64_element_kernel"] = _fp64_leg(kind, 2, T, k1 / calls)
+        else:
+            tp = _two_pass_ms(ef, torch, plan, tn, None, K, M, steps, stream)
+            leg["two_pass"] = {"ms_per_step": tp, "tuned_speedup": tp / ms}
         out[name] = leg
         plan.close()
         del K, M
