@@ -67,7 +67,7 @@ ADJOINT_FP64_OPS_PER_TET = 9 + 18 + 12 + 9 + 4 + 2 + 6 + 9 + 17 + 30 + 6 + 4 + 2
 ADJOINT_INT_PIPE_OPS_PER_TET = 6 + 6 + 4 + 2 + 4 + 6 + 1 + 3 + 9 + 11 + 12 + 9
 ADJOINT_FP64_PIPE_OPS_PER_TET = ADJOINT_FP64_OPS_PER_TET - ADJOINT_INT_PIPE_OPS_PER_TET
 # executed FP64 instructions per tetrahedron of the adjoint kernel (ncu sass
-# counters on the 24^3 cube: 39 DADD, 123 DFMA, 1 DMUL)
+# counters on the 24^3 cube: 1 DADD, 161 DFMA, 1 DMUL)
 ADJOINT_FP64_EXECUTED_PER_TET = 163
 # DRAM bytes (read + write) per element of the Nedelec-3D element kernel of
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
@@ -177,12 +177,14 @@ class ClockSampler:
 # divided by its elements; every FP64 warp instruction had all 32 lanes on):
 # (kind, dim) -> DADD, DFMA, DMUL. Measured on the 24^3 cube (3D) and the
 # level-5 L-shape (2D); the counts do not depend on the mesh. No DMUL: the
-# products run on the integer pipes.
+# products run on the integer pipes; the additions are DFMAs with a
+# per-thread 1.0 (csrc/ef_fp64.cuh), which run at the FP64 pipe's full rate
+# where DADD runs at 84 % of it.
 ELEMENT_KERNEL_FP64_EXECUTED = {
-    (2, 3): {"dadd": 47, "dfma": 45, "dmul": 0},
-    (1, 3): {"dadd": 29, "dfma": 27, "dmul": 0},
-    (1, 2): {"dadd": 14, "dfma": 11, "dmul": 0},
-    (2, 2): {"dadd": 20, "dfma": 11, "dmul": 0},
+    (2, 3): {"dadd": 0, "dfma": 92, "dmul": 0},
+    (1, 3): {"dadd": 0, "dfma": 56, "dmul": 0},
+    (1, 2): {"dadd": 0, "dfma": 25, "dmul": 0},
+    (2, 2): {"dadd": 1, "dfma": 30, "dmul": 0},
 }
 ELEMENT_KERNEL_FP64_MIX = ELEMENT_KERNEL_FP64_EXECUTED[(2, 3)]
 

@@ -35,15 +35,15 @@ constexpr int ADJ_TPB = 256;
 // integer pipes, or FpMul): no product is contracted into an FMA, so both give
 // the same bits.
 template <class MUL>
-__device__ __forceinline__ void adjoint_element(MUL& mul, const double (&p)[4][3], double sigma, const double (&ut)[6],
-                                                const double (&vt)[6], bool& degenerate, double& J1,
-                                                double (&gcol)[3][3])
+__device__ __forceinline__ void adjoint_element(MUL& mul, const FpK& f, const double (&p)[4][3], double sigma,
+                                                const double (&ut)[6], const double (&vt)[6], bool& degenerate,
+                                                double& J1, double (&gcol)[3][3])
 {
     double B[3][3];   // B[row][col], col i = e_{i+1}
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) B[c][i] = p[i + 1][c] - p[0][c];
+        for (int c = 0; c < 3; c++) B[c][i] = f.sub(p[i + 1][c], p[0][c]);
     double H[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -65,25 +65,26 @@ __device__ __forceinline__ void adjoint_element(MUL& mul, const double (&p)[4][3
     const double cz = fma(B[0][1], B[1][2], -mul(B[1][1], B[0][2]));
     const double adet = abs_bits(fma(B[2][0], cz, fma(B[1][0], cy, mul(B[0][0], cx))));
     degenerate = not_positive(adet);
-    const double r = recip_positive(adet);
+    const double r = recip_positive(adet, f.one);
     const double r3 = mul(mul(r, r), r);
 
     // K part: aHa = a^T H a over the symmetric H
-    const double av[3] = {ut[1] - ut[2] + ut[4], ut[2] - ut[0] + ut[5], ut[0] - ut[1] + ut[3]};
+    const double av[3] = {f.add(f.sub(ut[1], ut[2]), ut[4]), f.add(f.sub(ut[2], ut[0]), ut[5]),
+                          f.add(f.sub(ut[0], ut[1]), ut[3])};
     const double aHa = fma(av[0], fma(H[0][0], av[0], twice(fma(H[0][1], av[1], mul(H[0][2], av[2])))),
                            fma(av[1], fma(H[1][1], av[1], twice(mul(H[1][2], av[2]))), mul(av[2], mul(H[2][2], av[2]))));
 
     // M part: C antisymmetric over the 4 nodes, edges (0,1),(0,2),(0,3),(1,2),(2,3),(3,1)
-    const double c0 = -(vt[0] + vt[1] + vt[2]);
-    const double c1 = vt[0] - vt[3] + vt[5];
-    const double c2 = vt[1] + vt[3] - vt[4];
-    const double c3 = vt[2] + vt[4] - vt[5];
-    const double beta[3] = {c1 - c0, c2 - c0, c3 - c0};
+    const double c0 = -f.add(f.add(vt[0], vt[1]), vt[2]);
+    const double c1 = f.add(f.sub(vt[0], vt[3]), vt[5]);
+    const double c2 = f.sub(f.add(vt[1], vt[3]), vt[4]);
+    const double c3 = f.sub(f.add(vt[2], vt[4]), vt[5]);
+    const double beta[3] = {f.sub(c1, c0), f.sub(c2, c0), f.sub(c3, c0)};
     // D = C S: row k, column j (node j+1): C_k,j+1 - C_k,0
     const double D[4][3] = {{vt[0], vt[1], vt[2]},
-                            {vt[0], vt[3] + vt[0], vt[0] - vt[5]},
-                            {vt[1] - vt[3], vt[1], vt[4] + vt[1]},
-                            {vt[5] + vt[2], vt[2] - vt[4], vt[2]}};
+                            {vt[0], f.add(vt[3], vt[0]), f.sub(vt[0], vt[5])},
+                            {f.sub(vt[1], vt[3]), vt[1], f.add(vt[4], vt[1])},
+                            {f.add(vt[5], vt[2]), f.sub(vt[2], vt[4]), vt[2]}};
     double P[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -164,20 +165,21 @@ __global__ void __launch_bounds__(ADJ_TPB, 2) k_adjoint_ned3(const int32_t* __re
     const int64_t e = (int64_t)blockIdx.x * ADJ_TPB + threadIdx.x;
     double Jloc = 0.0;
     if (e < T) {
+        const FpK f;
         double J1, gcol[3][3], sigma;
         bool degenerate;
         {
             double p[4][3], ut[6], vt[6];
             adjoint_load(elems, nodes, coeff, e2d, u, v, e, p, sigma, ut, vt);
             IntMul im;
-            adjoint_element(im, p, sigma, ut, vt, degenerate, J1, gcol);
+            adjoint_element(im, f, p, sigma, ut, vt, degenerate, J1, gcol);
             if (im.off) {
                 // the index through an opaque move: the loads are not merged with the ones above
                 int64_t e2 = e;
                 asm volatile("" : "+l"(e2));
                 adjoint_load(elems, nodes, coeff, e2d, u, v, e2, p, sigma, ut, vt);
                 FpMul fm;
-                adjoint_element(fm, p, sigma, ut, vt, degenerate, J1, gcol);
+                adjoint_element(fm, f, p, sigma, ut, vt, degenerate, J1, gcol);
             }
         }
         if (degenerate) atomicOr(status, ST_DEGENERATE);
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(ADJ_TPB, 2) k_adjoint_ned3(const int32_t* __re
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 gpart[(e * 4 + i + 1) * 3 + c] = gcol[i][c];
-                g0[c] = i == 0 ? -gcol[i][c] : g0[c] - gcol[i][c];
+                g0[c] = i == 0 ? -gcol[i][c] : f.sub(g0[c], gcol[i][c]);
             }
 #pragma unroll
         for (int c = 0; c < 3; c++) gpart[(e * 4) * 3 + c] = g0[c];

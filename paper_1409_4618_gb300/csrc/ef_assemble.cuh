@@ -2,6 +2,8 @@
 // local matrices; shared by every kernel that computes element matrices.
 #pragma once
 
+#include <type_traits>
+
 #include "ef_element.cuh"
 #include "ef_internal.cuh"
 
@@ -61,17 +63,17 @@ struct ScaledTraits {
     static constexpr int N = (VAR == NED3 || VAR == RT3) ? 12 : TriScaled<VAR == NED2 ? 2 : 0>::N;
 };
 
-template <int VAR, class MUL>
-__device__ __forceinline__ bool element_scaled(MUL& mul,
+template <int VAR, class MUL, class FK>
+__device__ __forceinline__ bool element_scaled(MUL& mul, const FK& f,
                                                const double (&p)[ElemTraits<VAR>::NV][ElemTraits<VAR>::DIM],
                                                double sigmaK, double sigmaM, double (&s)[ScaledTraits<VAR>::N])
 {
     if constexpr (VAR == NED3)
-        return ned3_scaled(mul, p, sigmaK, sigmaM, s);
+        return ned3_scaled(mul, f, p, sigmaK, sigmaM, s);
     else if constexpr (VAR == RT3)
-        return rt3_scaled(mul, p, sigmaK, sigmaM, s);
+        return rt3_scaled(mul, f, p, sigmaK, sigmaM, s);
     else
-        return tri_scaled<VAR == NED2 ? 2 : 0>(mul, p, sigmaK, sigmaM, s);
+        return tri_scaled<VAR == NED2 ? 2 : 0>(mul, f, p, sigmaK, sigmaM, s);
 }
 
 // Signed local K, M upper triangles of element e, K times its coefficient in
@@ -82,14 +84,17 @@ __device__ __forceinline__ bool element_scaled(MUL& mul,
 // the FP64 multiply from its data loaded again (so that none of it has to
 // stay in registers meanwhile). Either way the entries are those of the
 // routine with FP64 products, bit for bit, so a kernel may take whichever
-// form runs faster in it (the integer form needs more registers).
-template <int VAR, bool INT_MUL = true>
+// form runs faster in it (the integer form needs more registers). Likewise
+// REG_CONST: additions as FMAs with per-thread constants (FpK, the FP64
+// pipe's full rate) or plain (FpLit, three registers fewer); same bits.
+template <int VAR, bool INT_MUL = true, bool REG_CONST = true>
 __device__ __forceinline__ bool compute_element(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
                                                 const double* __restrict__ coeffK, const double* __restrict__ coeffM,
                                                 int64_t e, double (&Kq)[ElemTraits<VAR>::NP],
                                                 double (&Mq)[ElemTraits<VAR>::NP])
 {
     using E = ElemTraits<VAR>;
+    const std::conditional_t<REG_CONST, FpK, FpLit> f;
     double s[ScaledTraits<VAR>::N];
     uint32_t neg;
     bool bad;
@@ -100,26 +105,26 @@ __device__ __forceinline__ bool compute_element(const int32_t* __restrict__ elem
         neg = sign_bits<VAR>(g);
         if constexpr (!INT_MUL) {
             FpMul fm;
-            bad = element_scaled<VAR>(fm, p, sigmaK, sigmaM, s);
+            bad = element_scaled<VAR>(fm, f, p, sigmaK, sigmaM, s);
         } else {
             IntMul im;
-            bad = element_scaled<VAR>(im, p, sigmaK, sigmaM, s);
+            bad = element_scaled<VAR>(im, f, p, sigmaK, sigmaM, s);
             if (im.off) {
                 // the index through an opaque move: the loads are not merged with the ones above
                 int64_t e2 = e;
                 asm volatile("" : "+l"(e2));
                 load_element<VAR>(elems, nodes, coeffK, coeffM, e2, g, p, sigmaK, sigmaM);
                 FpMul fm;
-                bad = element_scaled<VAR>(fm, p, sigmaK, sigmaM, s);
+                bad = element_scaled<VAR>(fm, f, p, sigmaK, sigmaM, s);
             }
         }
     }
     if constexpr (VAR == NED3)
-        ned3_entries(s, neg, Kq, Mq);
+        ned3_entries(f, s, neg, Kq, Mq);
     else if constexpr (VAR == RT3)
-        rt3_entries(s, neg, Kq, Mq);
+        rt3_entries(f, s, neg, Kq, Mq);
     else
-        tri_entries<VAR == NED2 ? 2 : 0>(s, neg, Kq, Mq);
+        tri_entries<VAR == NED2 ? 2 : 0>(f, s, neg, Kq, Mq);
     return bad;
 }
 

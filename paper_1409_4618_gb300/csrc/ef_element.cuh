@@ -31,6 +31,7 @@
 
 #include <stdint.h>
 
+#include "ef_fp64.cuh"
 #include "ef_intmul.cuh"
 
 namespace ef {
@@ -120,13 +121,14 @@ __device__ __forceinline__ bool not_positive(double x)
 // rcp.approx.ftz.f64, relative error below 2^-22): two steps reach double
 // precision to about one ulp. Four DFMA on the FP64 pipe, which bounds the
 // element kernels, against the longer sequence of the IEEE division. Callers
-// flag x outside the positive normals as degenerate (not_positive).
-__device__ __forceinline__ double recip_positive(double x)
+// flag x outside the positive normals as degenerate (not_positive); one = 1
+// from a per-thread register keeps the FMAs at the pipe's full rate (FpK).
+__device__ __forceinline__ double recip_positive(double x, double one = 1.0)
 {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    y = fma(y, fma(-x, y, 1.0), y);
-    return fma(y, fma(-x, y, 1.0), y);
+    y = fma(y, fma(-x, y, one), y);
+    return fma(y, fma(-x, y, one), y);
 }
 
 // ---- 3D Nedelec: 21 + 21 upper entries ---------------------------------------
@@ -135,13 +137,13 @@ __device__ __forceinline__ double recip_positive(double x)
 // (sigma_M / (120|det|)) adj(H) (upper triangles, order 11, 22, 33, 12, 13, 23).
 // MUL forms the products (IntMul on the integer pipes, or FpMul); true if
 // degenerate.
-template <class MUL>
-__device__ __forceinline__ bool ned3_scaled(MUL& mul, const double (&p)[4][3], double sigmaK, double sigmaM,
-                                            double (&s)[12])
+template <class MUL, class FK>
+__device__ __forceinline__ bool ned3_scaled(MUL& mul, const FK& f, const double (&p)[4][3], double sigmaK,
+                                            double sigmaM, double (&s)[12])
 {
-    const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
-    const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
-    const double e3x = p[3][0] - p[0][0], e3y = p[3][1] - p[0][1], e3z = p[3][2] - p[0][2];
+    const double e1x = f.sub(p[1][0], p[0][0]), e1y = f.sub(p[1][1], p[0][1]), e1z = f.sub(p[1][2], p[0][2]);
+    const double e2x = f.sub(p[2][0], p[0][0]), e2y = f.sub(p[2][1], p[0][1]), e2z = f.sub(p[2][2], p[0][2]);
+    const double e3x = f.sub(p[3][0], p[0][0]), e3y = f.sub(p[3][1], p[0][1]), e3z = f.sub(p[3][2], p[0][2]);
     const double H11 = fma(e1z, e1z, fma(e1y, e1y, mul(e1x, e1x)));
     const double H22 = fma(e2z, e2z, fma(e2y, e2y, mul(e2x, e2x)));
     const double H33 = fma(e3z, e3z, fma(e3y, e3y, mul(e3x, e3x)));
@@ -160,7 +162,7 @@ __device__ __forceinline__ bool ned3_scaled(MUL& mul, const double (&p)[4][3], d
     const double cx = fma(e2y, e3z, -mul(e2z, e3y)), cy = fma(e2z, e3x, -mul(e2x, e3z)), cz = fma(e2x, e3y, -mul(e2y, e3x));
     const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, mul(e1x, cx))));
     const bool bad = not_positive(adet);
-    const double r = recip_positive(adet);
+    const double r = recip_positive(adet, f.one);
     const double srK = mul(sigmaK, r), srM = mul(sigmaM, r);
 
     // K_kl = (2 sigma / (3|det|)) w_k . w_l
@@ -174,14 +176,16 @@ __device__ __forceinline__ bool ned3_scaled(MUL& mul, const double (&p)[4][3], d
 }
 
 // The 21 + 21 signed entries from h and g: additions and FMAs only.
-__device__ __forceinline__ void ned3_entries(const double (&s)[12], uint32_t neg, double (&Kq)[21], double (&Mq)[21])
+template <class FK>
+__device__ __forceinline__ void ned3_entries(const FK& f, const double (&s)[12], uint32_t neg, double (&Kq)[21],
+                                             double (&Mq)[21])
 {
     const double h11 = s[0], h22 = s[1], h33 = s[2], h12 = s[3], h13 = s[4], h23 = s[5];
-    const double k03 = h33 - h23, k04 = h13 - h12, k05 = h23 - h22;
-    const double k13 = h13 - h33, k14 = h11 - h13, k15 = h12 - h23;
-    const double k23 = h23 - h13, k24 = h12 - h11, k25 = h22 - h12;
-    const double k00 = k03 - k05, k11 = k14 - k13, k22 = k25 - k24;
-    const double k01 = k04 - k03, k02 = k05 - k04, k12 = k15 - k14;
+    const double k03 = f.sub(h33, h23), k04 = f.sub(h13, h12), k05 = f.sub(h23, h22);
+    const double k13 = f.sub(h13, h33), k14 = f.sub(h11, h13), k15 = f.sub(h12, h23);
+    const double k23 = f.sub(h23, h13), k24 = f.sub(h12, h11), k25 = f.sub(h22, h12);
+    const double k00 = f.sub(k03, k05), k11 = f.sub(k14, k13), k22 = f.sub(k25, k24);
+    const double k01 = f.sub(k04, k03), k02 = f.sub(k05, k04), k12 = f.sub(k15, k14);
     // M: Whitney-form combinations of g = sigma/(120|det|) adj(H) (the
     // scaled Gram matrix of grad lambda_1..3). With p_ab = -G_ab for the six
     // node pairs (the row of node 0 from the zero row sums), S_a = G_aa, and
@@ -192,12 +196,13 @@ __device__ __forceinline__ void ned3_entries(const double (&s)[12], uint32_t neg
     // +-(2 S_s - (p_uv + o(uv))); disjoint edges (a,b), (c,d): p_ad + p_bc -
     // p_ac - p_bd, a difference of two o's. 41 operations after the scaling.
     const double g11 = s[6], g22 = s[7], g33 = s[8], g12 = s[9], g13 = s[10], g23 = s[11];
-    const double p01 = g11 + g12 + g13, p02 = g12 + g22 + g23, p03 = g13 + g23 + g33;   // p12 = -g12, ...
-    const double S0 = p01 + p02 + p03;
-    const double oA = p01 - g23, oB = p02 - g13, oC = p03 - g12;   // {01,23}, {02,13}, {03,12}
-    const double QA = oB + oC, QB = oA + oC, QC = oA + oB;
-    const double r01 = oA + p01, r02 = oB + p02, r03 = oC + p03;
-    const double r12 = oC - g12, r13 = oB - g13, r23 = oA - g23;
+    const double p01 = f.add(f.add(g11, g12), g13), p02 = f.add(f.add(g12, g22), g23),
+                 p03 = f.add(f.add(g13, g23), g33);   // p12 = -g12, ...
+    const double S0 = f.add(f.add(p01, p02), p03);
+    const double oA = f.sub(p01, g23), oB = f.sub(p02, g13), oC = f.sub(p03, g12);   // {01,23}, {02,13}, {03,12}
+    const double QA = f.add(oB, oC), QB = f.add(oA, oC), QC = f.add(oA, oB);
+    const double r01 = f.add(oA, p01), r02 = f.add(oB, p02), r03 = f.add(oC, p03);
+    const double r12 = f.sub(oC, g12), r13 = f.sub(oB, g13), r23 = f.sub(oA, g23);
 
     // order: (0,0)..(0,5), (1,1)..(1,5), (2,2)..(2,5), (3,3)..(3,5), (4,4),(4,5), (5,5)
     Kq[0] = k00; Kq[1] = k01; Kq[2] = k02; Kq[3] = k03; Kq[4] = k04; Kq[5] = k05;
@@ -208,27 +213,28 @@ __device__ __forceinline__ void ned3_entries(const double (&s)[12], uint32_t neg
     Kq[20] = h22;
 
     // local edges 0..5 = (0,1), (0,2), (0,3), (1,2), (2,3), (3,1)
-    Mq[0] = twice(fma(3.0, p01, QA));
-    Mq[1] = fma(2.0, S0, -r12);
-    Mq[2] = fma(2.0, S0, -r13);
-    Mq[3] = fma(-2.0, g11, r02);
-    Mq[4] = oC - oB;
-    Mq[5] = fma(2.0, g11, -r03);
-    Mq[6] = twice(fma(3.0, p02, QB));
-    Mq[7] = fma(2.0, S0, -r23);
-    Mq[8] = fma(2.0, g22, -r01);
-    Mq[9] = fma(-2.0, g22, r03);
-    Mq[10] = oA - oC;
-    Mq[11] = twice(fma(3.0, p03, QC));
-    Mq[12] = oB - oA;
-    Mq[13] = fma(2.0, g33, -r02);
-    Mq[14] = fma(-2.0, g33, r01);
-    Mq[15] = twice(fma(-3.0, g12, QC));
-    Mq[16] = fma(-2.0, g22, r13);
-    Mq[17] = fma(-2.0, g11, r23);
-    Mq[18] = twice(fma(-3.0, g23, QA));
-    Mq[19] = fma(-2.0, g33, r12);
-    Mq[20] = twice(fma(-3.0, g13, QB));
+    const double two = f.two, three = f.three;
+    Mq[0] = twice(fma(three, p01, QA));
+    Mq[1] = fma(two, S0, -r12);
+    Mq[2] = fma(two, S0, -r13);
+    Mq[3] = fma(-two, g11, r02);
+    Mq[4] = f.sub(oC, oB);
+    Mq[5] = fma(two, g11, -r03);
+    Mq[6] = twice(fma(three, p02, QB));
+    Mq[7] = fma(two, S0, -r23);
+    Mq[8] = fma(two, g22, -r01);
+    Mq[9] = fma(-two, g22, r03);
+    Mq[10] = f.sub(oA, oC);
+    Mq[11] = twice(fma(three, p03, QC));
+    Mq[12] = f.sub(oB, oA);
+    Mq[13] = fma(two, g33, -r02);
+    Mq[14] = fma(-two, g33, r01);
+    Mq[15] = twice(fma(-three, g12, QC));
+    Mq[16] = fma(-two, g22, r13);
+    Mq[17] = fma(-two, g11, r23);
+    Mq[18] = twice(fma(-three, g23, QA));
+    Mq[19] = fma(-two, g33, r12);
+    Mq[20] = twice(fma(-three, g13, QB));
 
     // signs s_k s_l on the off-diagonal pairs
     int q = 0;
@@ -245,13 +251,13 @@ __device__ __forceinline__ void ned3_entries(const double (&s)[12], uint32_t neg
 // ---- 3D RT0: 10 + 10 upper entries (DOF k <-> opposite vertex 3-k) ---------
 // First part (every product): s = (H11, H22, H33, H12, H13, H23, m20, c0s, q1,
 // q2, q3, kv) in the notation below.
-template <class MUL>
-__device__ __forceinline__ bool rt3_scaled(MUL& mul, const double (&p)[4][3], double sigmaK, double sigmaM,
-                                           double (&s)[12])
+template <class MUL, class FK>
+__device__ __forceinline__ bool rt3_scaled(MUL& mul, const FK& f, const double (&p)[4][3], double sigmaK,
+                                           double sigmaM, double (&s)[12])
 {
-    const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1], e1z = p[1][2] - p[0][2];
-    const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1], e2z = p[2][2] - p[0][2];
-    const double e3x = p[3][0] - p[0][0], e3y = p[3][1] - p[0][1], e3z = p[3][2] - p[0][2];
+    const double e1x = f.sub(p[1][0], p[0][0]), e1y = f.sub(p[1][1], p[0][1]), e1z = f.sub(p[1][2], p[0][2]);
+    const double e2x = f.sub(p[2][0], p[0][0]), e2y = f.sub(p[2][1], p[0][1]), e2z = f.sub(p[2][2], p[0][2]);
+    const double e3x = f.sub(p[3][0], p[0][0]), e3y = f.sub(p[3][1], p[0][1]), e3z = f.sub(p[3][2], p[0][2]);
     const double H11 = fma(e1z, e1z, fma(e1y, e1y, mul(e1x, e1x)));
     const double H22 = fma(e2z, e2z, fma(e2y, e2y, mul(e2x, e2x)));
     const double H33 = fma(e3z, e3z, fma(e3y, e3y, mul(e3x, e3x)));
@@ -261,11 +267,11 @@ __device__ __forceinline__ bool rt3_scaled(MUL& mul, const double (&p)[4][3], do
     const double cx = fma(e2y, e3z, -mul(e2z, e3y)), cy = fma(e2z, e3x, -mul(e2x, e3z)), cz = fma(e2x, e3y, -mul(e2y, e3x));
     const double adet = abs_bits(fma(e1z, cz, fma(e1y, cy, mul(e1x, cx))));
     const bool bad = not_positive(adet);
-    const double r = recip_positive(adet);
+    const double r = recip_positive(adet, f.one);
     const double srK = mul(sigmaK, r), srM = mul(sigmaM, r);
     // M: sigma/(120|det|) [c0 - 5 (S.y_a + S.y_b) + 20 y_a.y_b]
-    const double r1 = H11 + H12 + H13, r2 = H12 + H22 + H23, r3 = H13 + H23 + H33;
-    const double c0 = (r1 + r2 + r3) + (H11 + H22 + H33);
+    const double r1 = f.add(f.add(H11, H12), H13), r2 = f.add(f.add(H12, H22), H23), r3 = f.add(f.add(H13, H23), H33);
+    const double c0 = f.add(f.add(f.add(r1, r2), r3), f.add(f.add(H11, H22), H33));
     const double cM = mul(srM, 1.0 / 120.0);
     const double m5 = mul(-5.0, cM);
     s[0] = H11; s[1] = H22; s[2] = H33; s[3] = H12; s[4] = H13; s[5] = H23;
@@ -276,21 +282,23 @@ __device__ __forceinline__ bool rt3_scaled(MUL& mul, const double (&p)[4][3], do
     return bad;
 }
 
-__device__ __forceinline__ void rt3_entries(const double (&s)[12], uint32_t neg, double (&Kq)[10], double (&Mq)[10])
+template <class FK>
+__device__ __forceinline__ void rt3_entries(const FK& f, const double (&s)[12], uint32_t neg, double (&Kq)[10],
+                                            double (&Mq)[10])
 {
     const double H11 = s[0], H22 = s[1], H33 = s[2], H12 = s[3], H13 = s[4], H23 = s[5];
     const double m20 = s[6], c0s = s[7], q1 = s[8], q2 = s[9], q3 = s[10], kv = s[11];
-    const double t1 = c0s + q1, t2 = c0s + q2, t3 = c0s + q3;
+    const double t1 = f.add(c0s, q1), t2 = f.add(c0s, q2), t3 = f.add(c0s, q3);
     // DOF k <-> opposite vertex a = 3 - k; vertex 0 has y_0 = 0
     // (0,0):a=3  (0,1):3,2  (0,2):3,1  (0,3):3,0  (1,1):2  (1,2):2,1  (1,3):2,0  (2,2):1  (2,3):1,0  (3,3):0
-    Mq[0] = fma(m20, H33, t3 + q3);
-    Mq[1] = fma(m20, H23, t3 + q2);
-    Mq[2] = fma(m20, H13, t3 + q1);
+    Mq[0] = fma(m20, H33, f.add(t3, q3));
+    Mq[1] = fma(m20, H23, f.add(t3, q2));
+    Mq[2] = fma(m20, H13, f.add(t3, q1));
     Mq[3] = t3;
-    Mq[4] = fma(m20, H22, t2 + q2);
-    Mq[5] = fma(m20, H12, t2 + q1);
+    Mq[4] = fma(m20, H22, f.add(t2, q2));
+    Mq[5] = fma(m20, H12, f.add(t2, q1));
     Mq[6] = t2;
-    Mq[7] = fma(m20, H11, t1 + q1);
+    Mq[7] = fma(m20, H11, f.add(t1, q1));
     Mq[8] = t1;
     Mq[9] = c0s;
     int q = 0;
@@ -312,24 +320,24 @@ struct TriScaled {
     static constexpr int N = VAR == 0 ? 8 : 4;
 };
 
-template <int VAR, class MUL>
-__device__ __forceinline__ bool tri_scaled(MUL& mul, const double (&p)[3][2], double sigmaK, double sigmaM,
-                                           double (&s)[TriScaled<VAR>::N])
+template <int VAR, class MUL, class FK>
+__device__ __forceinline__ bool tri_scaled(MUL& mul, const FK& f, const double (&p)[3][2], double sigmaK,
+                                           double sigmaM, double (&s)[TriScaled<VAR>::N])
 {
-    const double e1x = p[1][0] - p[0][0], e1y = p[1][1] - p[0][1];
-    const double e2x = p[2][0] - p[0][0], e2y = p[2][1] - p[0][1];
+    const double e1x = f.sub(p[1][0], p[0][0]), e1y = f.sub(p[1][1], p[0][1]);
+    const double e2x = f.sub(p[2][0], p[0][0]), e2y = f.sub(p[2][1], p[0][1]);
     const double H11 = fma(e1y, e1y, mul(e1x, e1x)), H22 = fma(e2y, e2y, mul(e2x, e2x)),
                  H12 = fma(e1y, e2y, mul(e1x, e2x));
     const double adet = abs_bits(fma(e1x, e2y, -mul(e1y, e2x)));
     const bool bad = not_positive(adet);
-    const double r = recip_positive(adet);
+    const double r = recip_positive(adet, f.one);
     const double srK = mul(sigmaK, r), srM = mul(sigmaM, r);
     const double cM = mul(srM, 1.0 / 24.0);
     const double kv = twice(srK);   // (div eta)^2 |Khat| = 4/2 (RT); curl^2 |Khat| = 4/2 (Ned)
     if constexpr (VAR == 0) {
         // RT0: sigma/(24|det|) [c0 - 4 (S.y_a + S.y_b) + 12 y_a.y_b], DOF k <-> vertex k
-        const double r1 = H11 + H12, r2 = H12 + H22;
-        const double c0 = (r1 + r2) + (H11 + H22);
+        const double r1 = f.add(H11, H12), r2 = f.add(H12, H22);
+        const double c0 = f.add(f.add(r1, r2), f.add(H11, H22));
         const double m4 = mul(-4.0, cM);
         s[0] = H11; s[1] = H12; s[2] = H22;
         s[3] = mul(12.0, cM);
@@ -344,32 +352,33 @@ __device__ __forceinline__ bool tri_scaled(MUL& mul, const double (&p)[3][2], do
     return bad;
 }
 
-template <int VAR>
-__device__ __forceinline__ void tri_entries(const double (&s)[TriScaled<VAR>::N], uint32_t neg, double (&Kq)[6],
-                                            double (&Mq)[6])
+template <int VAR, class FK>
+__device__ __forceinline__ void tri_entries(const FK& f, const double (&s)[TriScaled<VAR>::N], uint32_t neg,
+                                            double (&Kq)[6], double (&Mq)[6])
 {
     double kv;
     if constexpr (VAR == 0) {
         const double H11 = s[0], H12 = s[1], H22 = s[2], m12 = s[3], c0s = s[4], q1 = s[5], q2 = s[6];
         kv = s[7];
-        const double t1 = c0s + q1, t2 = c0s + q2;
-        Mq[0] = c0s;                          // (0,0)
-        Mq[1] = t1;                           // (0,1)
-        Mq[2] = t2;                           // (0,2)
-        Mq[3] = fma(m12, H11, t1 + q1);       // (1,1)
-        Mq[4] = fma(m12, H12, t1 + q2);       // (1,2)
-        Mq[5] = fma(m12, H22, t2 + q2);       // (2,2)
+        const double t1 = f.add(c0s, q1), t2 = f.add(c0s, q2);
+        Mq[0] = c0s;                              // (0,0)
+        Mq[1] = t1;                               // (0,1)
+        Mq[2] = t2;                               // (0,2)
+        Mq[3] = fma(m12, H11, f.add(t1, q1));     // (1,1)
+        Mq[4] = fma(m12, H12, f.add(t1, q2));     // (1,2)
+        Mq[5] = fma(m12, H22, f.add(t2, q2));     // (2,2)
     } else {
         const double g11 = s[0], g22 = s[1], g12 = s[2];
         kv = s[3];
-        const double g01 = -(g11 + g12), g02 = -(g12 + g22);
-        const double g00 = -(g01 + g02);
-        Mq[0] = twice(g11 + g22 - g12);
-        Mq[1] = fma(-2.0, g01, g02 - g22 + g12);
-        Mq[2] = fma(-2.0, g02, g12 - g11 + g01);
-        Mq[3] = twice(g22 + g00 - g02);
-        Mq[4] = fma(-2.0, g12, g01 - g00 + g02);
-        Mq[5] = twice(g00 + g11 - g01);
+        const double g01 = -f.add(g11, g12), g02 = -f.add(g12, g22);
+        const double g00 = -f.add(g01, g02);
+        const double two = f.two;
+        Mq[0] = twice(f.sub(f.add(g11, g22), g12));
+        Mq[1] = fma(-two, g01, f.add(f.sub(g02, g22), g12));
+        Mq[2] = fma(-two, g02, f.add(f.sub(g12, g11), g01));
+        Mq[3] = twice(f.sub(f.add(g22, g00), g02));
+        Mq[4] = fma(-two, g12, f.add(f.sub(g01, g00), g02));
+        Mq[5] = twice(f.sub(f.add(g00, g11), g01));
     }
     int q = 0;
 #pragma unroll

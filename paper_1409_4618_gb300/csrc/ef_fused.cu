@@ -275,6 +275,16 @@ constexpr bool fused_int_mul()
     return VAR != RT3;
 }
 
+// Additions as FMAs with per-thread constants (full FP64 rate) in the 3D
+// kernels; the 2D ones, held to 40 registers, keep plain additions (the
+// per-thread constants cost them spills: level-11 L-shape 2.19 / 2.26 ms
+// against 2.18 / 2.23 ms)
+template <int VAR>
+constexpr bool fused_reg_const()
+{
+    return VAR == NED3 || VAR == RT3;
+}
+
 template <int VAR, int BE>
 __global__ void __launch_bounds__(BE, (fused_min_blocks<VAR, BE>())) k_fused(const int32_t* __restrict__ elems, const double* __restrict__ nodes,
                                               const double* __restrict__ coeff, int64_t T,
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(BE, (fused_min_blocks<VAR, BE>())) k_fused(con
 #pragma unroll
         for (int q = 0; q < E::NP; q++) pos[q] = __ldg(si + q * BE);
         double Kq[E::NP], Mq[E::NP];
-        if (compute_element<VAR, fused_int_mul<VAR>()>(elems, nodes, coeff, coeff, e, Kq, Mq))
+        if (compute_element<VAR, fused_int_mul<VAR>(), fused_reg_const<VAR>()>(elems, nodes, coeff, coeff, e, Kq, Mq))
             atomicOr(status, ST_DEGENERATE);
 #pragma unroll
         for (int q = 0; q < E::NP; q++) {

@@ -8,10 +8,14 @@
 // (rounded up to a multiple of UNROLL); with CHAINS chains per thread and 32
 // warps per SM the latency is hidden, so the time is set by the issue rate.
 // The result is lane operations per second (a DFMA counts as one operation,
-// as in the element kernels' op counts).
+// as in the element kernels' op counts). The operands other than the chain
+// value are per-thread registers (ef_fp64.cuh): a literal or warp-uniform
+// operand would hold a DFMA to 84 % of the pipe's rate, the rate DADD and
+// DMUL run at in any form.
 //
 // ef_int_mul_check compares the integer-pipe multiply with the FP64 multiply
 // instruction bit for bit on generated operands.
+#include "ef_fp64.cuh"
 #include "ef_internal.cuh"
 #include "ef_intmul.cuh"
 
@@ -29,7 +33,7 @@ __global__ void __launch_bounds__(PROBE_TPB) k_fp64_probe(int rounds, double see
     double a[CHAINS];
 #pragma unroll
     for (int i = 0; i < CHAINS; i++) a[i] = seed + 1e-3 * threadIdx.x + i;
-    const double m = 1.0 + 1e-12, c = 1e-15;
+    const double m = per_thread(1.0 + 1e-12), c = per_thread(1e-15);
     IntMul im;
     // UNROLL rounds per loop trip, so that the loop's own integer work is small
     for (int it = 0; it < rounds; it++) {
