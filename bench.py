@@ -73,7 +73,7 @@ ADJOINT_FP64_EXECUTED_PER_TET = 163
 # the two-pass schedule, from ncu dram__bytes_{read,write}.sum of one launch
 # on the 48^3 cube (663,552 tets); the launch's traffic grows in proportion
 # to the elements.
-ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (74.955520e6 + 176.536064e6) / 663552
+ELEMENT_KERNEL_DRAM_BYTES_PER_TET = (75.176192e6 + 177.140224e6) / 663552
 
 
 def _peaks():
@@ -206,7 +206,8 @@ def run_fp64_probe(gpu_index: int) -> dict:
 
     rates = {}
     with ClockSampler(gpu_index) as clk:
-        for name, op in (("dfma", 0), ("dadd", 1), ("dmul", 2), ("int_mul", 3), ("dfma_and_int_mul", 4)):
+        for name, op in (("dfma", 0), ("dadd", 1), ("dmul", 2), ("int_mul", 3), ("dfma_and_int_mul", 4),
+                         ("dfma_literal_operands", 5), ("add_as_dfma", 6)):
             best = None
             for _ in range(3):
                 r, ms = ef.ef_fp64_probe(op, FP64_PROBE_ITERS)

@@ -3,8 +3,9 @@
 // of the integer-pipe multiply (ef_intmul.cuh) alone and beside the FP64 pipe.
 //
 // Every thread runs CHAINS independent dependency chains of one operation
-// (DFMA, DADD, DMUL, the integer-pipe multiply, or DFMA in half of the chains
-// and the integer-pipe multiply in the other half), `iters` operations each
+// (DFMA, DADD, DMUL, the integer-pipe multiply, DFMA in half of the chains
+// and the integer-pipe multiply in the other half, DFMA with literal
+// operands, or an addition as a DFMA with a per-thread 1.0), `iters` each
 // (rounded up to a multiple of UNROLL); with CHAINS chains per thread and 32
 // warps per SM the latency is hidden, so the time is set by the issue rate.
 // The result is lane operations per second (a DFMA counts as one operation,
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(PROBE_TPB) k_fp64_probe(int rounds, double see
     double a[CHAINS];
 #pragma unroll
     for (int i = 0; i < CHAINS; i++) a[i] = seed + 1e-3 * threadIdx.x + i;
-    const double m = per_thread(1.0 + 1e-12), c = per_thread(1e-15);
+    const double m = per_thread(1.0 + 1e-12), c = per_thread(1e-15), one = per_thread(1.0);
     IntMul im;
     // UNROLL rounds per loop trip, so that the loop's own integer work is small
     for (int it = 0; it < rounds; it++) {
@@ -46,6 +47,8 @@ __global__ void __launch_bounds__(PROBE_TPB) k_fp64_probe(int rounds, double see
                 if (OP == 2) a[i] = a[i] * m;
                 if (OP == 3) a[i] = im(a[i], m);
                 if (OP == 4) a[i] = i < CHAINS / 2 ? fma(a[i], m, c) : im(a[i], m);
+                if (OP == 5) a[i] = fma(a[i], 1.0 + 1e-12, 1e-15);   // literal operands
+                if (OP == 6) a[i] = fma(a[i], one, c);               // a + c at the full rate
             }
     }
     double s = 0;
@@ -116,7 +119,7 @@ using namespace ef;
 
 extern "C" int ef_fp64_probe(int op, int64_t iters, double* d_sink, double* ops_per_s, double* ms, void* stream)
 {
-    if (op < 0 || op > 4 || iters < 1 || !d_sink || !ops_per_s) return EF_ERR_ARG;
+    if (op < 0 || op > 6 || iters < 1 || !d_sink || !ops_per_s) return EF_ERR_ARG;
     int dev = 0, sms = 0;
     EF_CUDA(cudaGetDevice(&dev));
     EF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -134,6 +137,8 @@ extern "C" int ef_fp64_probe(int op, int64_t iters, double* d_sink, double* ops_
         if (op == 2) k_fp64_probe<2><<<grid, PROBE_TPB, 0, s>>>(n, 1.0, d_sink);
         if (op == 3) k_fp64_probe<3><<<grid, PROBE_TPB, 0, s>>>(n, 1.0, d_sink);
         if (op == 4) k_fp64_probe<4><<<grid, PROBE_TPB, 0, s>>>(n, 1.0, d_sink);
+        if (op == 5) k_fp64_probe<5><<<grid, PROBE_TPB, 0, s>>>(n, 1.0, d_sink);
+        if (op == 6) k_fp64_probe<6><<<grid, PROBE_TPB, 0, s>>>(n, 1.0, d_sink);
     };
     launch(rounds < 8 ? rounds : 8);   // warm-up
     cudaEventRecord(e0, s);

@@ -250,7 +250,8 @@ def ef_adjoint(plan, nodes, coeff, u, v, J=None, grad_nodes=None, grad_coeff=Non
 def ef_fp64_probe(op: int, iters: int, stream=None) -> tuple[float, float]:
     """(lane operations per second, ms) for op 0 = DFMA, 1 = DADD, 2 = DMUL,
     3 = the integer-pipe multiply, 4 = DFMA and the integer-pipe multiply in
-    half of the chains each."""
+    half of the chains each, 5 = DFMA with literal operands, 6 = an addition as
+    a DFMA with a per-thread 1.0."""
     sink = torch.zeros(1, dtype=torch.float64, device="cuda")
     rate, ms = C.c_double(), C.c_double()
     _check(load().ef_fp64_probe(int(op), int(iters), C.c_void_p(sink.data_ptr()), C.byref(rate), C.byref(ms),

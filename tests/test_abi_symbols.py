@@ -65,7 +65,7 @@ def test_argument_errors_need_no_gpu():
     assert lib.ef_batch_plan_create(1, 3, 0, None, None, None, None, ctypes.byref(h)) == ef.EF_ERR_ARG
     assert lib.ef_batch_plan_create(3, 3, 1, None, None, None, None, ctypes.byref(h)) == ef.EF_ERR_ARG
     rate, ms = ctypes.c_double(), ctypes.c_double()
-    assert lib.ef_fp64_probe(5, 10, ctypes.c_void_p(16), ctypes.byref(rate), ctypes.byref(ms), None) == ef.EF_ERR_ARG
+    assert lib.ef_fp64_probe(7, 10, ctypes.c_void_p(16), ctypes.byref(rate), ctypes.byref(ms), None) == ef.EF_ERR_ARG
     assert lib.ef_int_mul_check(ctypes.c_int64(-1), ctypes.c_uint64(0), ctypes.c_void_p(16), None) == ef.EF_ERR_ARG
     assert lib.ef_int_mul_check(ctypes.c_int64(10), ctypes.c_uint64(0), None, None) == ef.EF_ERR_ARG
     assert lib.ef_fp64_probe(0, 0, ctypes.c_void_p(16), ctypes.byref(rate), ctypes.byref(ms), None) == ef.EF_ERR_ARG
