@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2(const int32_t* __restrict__ el
         if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
         double s = 0.0;
         if (v) {
+            const FpK fk;   // the subtractions as full-rate DFMAs (same bits)
             FeAffine<VAR> fe;
             fe.setup(p, B, det, e2d, __ldg(signbits + e), v, e);
             // The points come in runs of n along the innermost collapsed
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2(const int32_t* __restrict__ el
                     double d2 = 0.0;
 #pragma unroll
                     for (int c = 0; c < DIM; c++) {
-                        const double d = __ldg(fq + c) - fma(fe.V[DIM - 1][c], xl, A[c]);
+                        const double d = fk.sub(__ldg(fq + c), fma(fe.V[DIM - 1][c], xl, A[c]));
                         d2 = fma(d, d, d2);
                     }
                     s = fma(table[q][3], d2, s);
@@ -656,12 +657,13 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2_deriv(const int32_t* __restric
         double d[3] = {0.0, 0.0, 0.0};
         if (v) fe_derivative<VAR>(B, 1.0 / det, e2d, __ldg(signbits + e), v, e, d);
         double s = 0.0;
+        const FpK fk;   // the subtractions as full-rate DFMAs (same bits)
         for (int q = 0; q < nq; q++) {
             const double* gq = g + ((int64_t)q * T + e) * NC;
             double d2 = 0.0;
 #pragma unroll
             for (int c = 0; c < NC; c++) {
-                const double x = __ldg(gq + c) - d[c];
+                const double x = fk.sub(__ldg(gq + c), d[c]);
                 d2 = fma(x, x, d2);
             }
             s = fma(table[q][3], d2, s);
