@@ -49,12 +49,14 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// CTAs per SM the kernel is compiled for: 64 registers per thread (8 CTAs
-// of 128 threads), so that the memory-bound sum tiles have 32 warps per SM;
-// the 3D Nedelec element matrices then spill about 100 bytes per thread.
-// Measured on the 256-mesh batch: 24.4 ms against 24.8 ms with 80 registers
-// (6 CTAs, no spills).
-constexpr int queue_min_blocks(int BE) { return BE == 128 ? 8 : 4; }
+// CTAs per SM the kernel is compiled for: 80 registers per thread (6 CTAs
+// of 128 threads), with the element tiles' products on the integer pipes and
+// their additions as full-rate DFMAs (the 3D Nedelec tiles spill about 150
+// bytes). Measured on the 256-mesh batch: 21.9 ms, against 23.4 ms with FP64
+// products at 64 registers (8 CTAs, the sum tiles' 32 warps per SM), 24.1 ms
+// with plain FP64 additions there as well, and 22.6 ms with integer products
+// at 96 registers (5 CTAs).
+constexpr int queue_min_blocks(int BE) { return BE == 128 ? 6 : 3; }
 
 __device__ __forceinline__ int find_segment(const QueueSegment* __restrict__ seg, int nseg, int64_t k)
 {
@@ -110,9 +112,7 @@ __global__ void __launch_bounds__(BE, MINB) k_queue(const QueueMesh* __restrict_
             if (e < g.hi) {
                 const double* coeff = nodes0 ? coeff0 : d.coeff;
                 double Kq[E::NP], Mq[E::NP];
-                // FP64 products in the 3D tiles: at the queue's 64 registers the integer
-                // form would spill
-                if (compute_element<VAR, ElemTraits<VAR>::DIM == 2>(d.elems, nodes, coeff, coeff, e, Kq, Mq))
+                if (compute_element<VAR, true, true>(d.elems, nodes, coeff, coeff, e, Kq, Mq))
                     atomicOr(status, ST_DEGENERATE);
 #pragma unroll
                 for (int q = 0; q < E::NP; q++) {
