@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(ITPB) k_fe_values(const int32_t* __restrict__ 
     FeAffine<VAR> fe;
     load_vertices<DIM>(elems, nodes, e, p);
     const double det = edge_frame<DIM>(p, B);
-    if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+    if (not_positive(abs_bits(det))) atomicOr(status, ST_DEGENERATE);
     fe.setup(p, B, det, e2d, __ldg(signbits + e), v, e);
     // runs of n points along the innermost collapsed coordinate, as in k_norm_l2
     const int n = r.n;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2(const int32_t* __restrict__ el
         double p[4][3], B[3][3];
         load_vertices<DIM>(elems, nodes, e, p);
         const double det = edge_frame<DIM>(p, B);
-        if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+        if (not_positive(abs_bits(det))) atomicOr(status, ST_DEGENERATE);
         double s = 0.0;
         if (v) {
             const FpK fk;   // the subtractions as full-rate DFMAs (same bits)
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(ITPB) k_load_local(const int32_t* __restrict__
     double p[4][3], B[3][3];
     load_vertices<DIM>(elems, nodes, e, p);
     const double det = edge_frame<DIM>(p, B);
-    if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+    if (not_positive(abs_bits(det))) atomicOr(status, ST_DEGENERATE);
     const double rdet = 1.0 / det;
     double m[DIM + 1][DIM];
 #pragma unroll
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(ITPB) k_load_deriv_local(const int32_t* __rest
     double p[4][3], B[3][3];
     load_vertices<DIM>(elems, nodes, e, p);
     const double det = edge_frame<DIM>(p, B);
-    if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+    if (not_positive(abs_bits(det))) atomicOr(status, ST_DEGENERATE);
     double gi[3] = {0.0, 0.0, 0.0};   // sum_q w_q g(x_q)
     for (int q = 0; q < nq; q++) {
         const double* gq = gf + ((int64_t)q * T + e) * NC;
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(ITPB) k_fe_curl(const int32_t* __restrict__ el
     double p[4][3], B[3][3];
     load_vertices<DIM>(elems, nodes, e, p);
     const double det = edge_frame<DIM>(p, B);
-    if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+    if (not_positive(abs_bits(det))) atomicOr(status, ST_DEGENERATE);
     double d[3];
     fe_derivative<VAR>(B, 1.0 / det, e2d, __ldg(signbits + e), v, e, d);
     if (VAR == NED3) {
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(ITPB) k_norm_l2_deriv(const int32_t* __restric
         double p[4][3], B[3][3];
         load_vertices<DIM>(elems, nodes, e, p);
         const double det = edge_frame<DIM>(p, B);
-        if (det == 0.0 || !isfinite(det)) atomicOr(status, ST_DEGENERATE);
+        if (not_positive(abs_bits(det))) atomicOr(status, ST_DEGENERATE);
         double d[3] = {0.0, 0.0, 0.0};
         if (v) fe_derivative<VAR>(B, 1.0 / det, e2d, __ldg(signbits + e), v, e, d);
         double s = 0.0;
