@@ -2,12 +2,13 @@
 // multiply instruction gives (IEEE 754 binary64, round to nearest, ties to
 // even), for use beside the FP64 pipe in the element kernels.
 //
-// On this GPU the FP64 pipe retires about 1.7 lane operations per SM per
-// clock, while the integer ALU and IMAD pipes retire 64 lanes each; the
-// element kernels keep the FP64 pipe busy and leave the integer pipes nearly
-// idle. A product computed here takes about 45 integer instructions and runs
-// beside the FP64 instructions of the same warps, so moving the products of
-// an element routine here shortens its critical resource by their share.
+// On this GPU the FP64 pipe retires at most 2 lane operations per SM per
+// clock (1.68 for DMUL), while the integer ALU and IMAD pipes retire 64
+// lanes each; the element kernels keep the FP64 pipe busy and leave the
+// integer pipes nearly idle. A product computed here takes about 50 integer
+// instructions (ALU and IMAD) and runs beside the FP64 instructions of the
+// same warps, so moving the products of an element routine here shortens its
+// critical resource by their share.
 //
 // Method (the textbook one for a binary floating-point product, e.g.
 // J.-M. Muller et al., Handbook of Floating-Point Arithmetic, 2nd ed., Sec.
