@@ -27,6 +27,12 @@
 // no floating-point work. |det B| enters only through r = 1/|det B|, with det B
 // from the triple product (accurate to cond(B) eps, also on nearly flat
 // elements) and r by Newton-Raphson steps (recip_positive).
+//
+// Each routine has a first part holding all of its products (the MUL policy:
+// IntMul on the integer pipes or FpMul, ef_intmul.cuh) and a second part of
+// additions and FMAs (the FK policy: FpK with full-rate DFMA forms or FpLit,
+// ef_fp64.cuh). Every combination gives the same bits; the kernels pick the
+// fastest for their register budget.
 #pragma once
 
 #include <stdint.h>
